@@ -1,0 +1,200 @@
+/*
+ * rosko.h - C ABI of the GB300 (sm_103a) row-skipping outer-product SpMM.
+ *
+ * Method (Rosko, arXiv 2307.03930): C = A.B with A an unstructured sparse
+ * weight matrix (M x K) and B a dense activation matrix (K x N).  Sec. 3: the
+ * outer product of column k of A with row k of B only touches the result rows
+ * m with A[m,k] != 0, so the other rows are skipped.  Sec. 4.1 / Alg. 1: A is
+ * packed per row panel into the nonzero values of each non-empty column (A_p),
+ * their panel-relative rows (loc_m), the column indices (col_ind) and the
+ * per-column counts (nnz).  Alg. 2 streams the packed columns, loads the
+ * matching row of B once and multiply-accumulates it into the register-
+ * resident C rows named by loc_m.
+ *
+ * Conventions shared by every call
+ *   - Pointers named *_dev are CUDA device pointers (or managed memory) on the
+ *     current device; *_host are host pointers.  The caller owns A, B, C and
+ *     the stream.  The library owns a packed handle until rosko_free.
+ *   - Matrices are row-major with an explicit leading dimension in ELEMENTS:
+ *     A[m*lda + k], B[k*ldb + n], C[m*ldc + n] (Alg. 1 indexes A as A[k + mK]).
+ *   - Every call is ordered on the given stream (NULL = legacy default stream)
+ *     and returns without synchronising, except where stated.
+ *   - Arguments are validated on the host before any launch; an invalid
+ *     argument returns ROSKO_ERR_INVALID_ARG and launches nothing.  Calls never
+ *     abort the process.  A kernel that detects an internal error (a bounded
+ *     wait that ran out, a corrupt packed stream) sets a bit in a per-device
+ *     status word read by rosko_device_status.
+ *   - Sizes are int64; the total nonzero count and the total number of packed
+ *     columns of one handle must stay below 2^31.
+ */
+#ifndef ROSKO_H_
+#define ROSKO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ROSKO_OK = 0,
+  ROSKO_ERR_INVALID_ARG = 1,  /* bad size, pointer, dtype, alignment or tile   */
+  ROSKO_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement   */
+  ROSKO_ERR_OOM = 3,          /* a device allocation failed                    */
+  ROSKO_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed             */
+  ROSKO_ERR_TIMEOUT = 5,      /* a bounded device wait ran out                 */
+  ROSKO_ERR_BAD_HANDLE = 6,   /* NULL, freed or corrupt packed handle          */
+  ROSKO_ERR_DEVICE = 7        /* a kernel reported an internal error           */
+} rosko_status;
+
+typedef enum {
+  ROSKO_F32 = 0,
+  ROSKO_BF16 = 1,
+  ROSKO_I8 = 2,
+  ROSKO_F64 = 3,  /* check mode only: FP64 accumulation of FP32-exact inputs */
+  ROSKO_I32 = 4
+} rosko_dtype;
+
+/* Opaque handle to a packed A (device buffers owned by the library). */
+typedef struct rosko_packed_s* rosko_packed_t;
+/* A cudaStream_t passed as an untyped pointer (NULL = legacy default stream). */
+typedef void* rosko_stream_t;
+
+typedef enum {
+  ROSKO_SCHED_ANALYTIC = 0,  /* closed-form tile rule (Sec. 4.2 re-derived)  */
+  ROSKO_SCHED_AUTOTUNE = 1,  /* per-shape timed search, cached               */
+  ROSKO_SCHED_LEARNED = 2,   /* MLP selector over problem features           */
+  ROSKO_SCHED_FORCED = 3     /* use the tile exactly as given                */
+} rosko_sched_mode;
+
+/*
+ * Tile parameters (Sec. 4.2 and Sec. 6 expose m_c, k_c, m_r, n_r).
+ *   m_r   rows per packed panel = C rows one warp holds in registers
+ *         (8, 16 or 32); fixed when A is packed.
+ *   n_r   C columns per CTA tile (32 lanes x columns per lane).
+ *   k_c   rows of B staged in shared memory per pipeline slab.
+ *   m_c   C rows per CTA = warps per CTA x m_r.
+ *   split_k  number of K ranges reduced into C with atomics (>= 1).
+ *   dense_split_pct  tensor-core dense-panel path for panels whose density
+ *         in percent is >= this value; 101 = never.
+ *   mode  a rosko_sched_mode.
+ * A field <= 0 means "library chooses" (except in ROSKO_SCHED_FORCED).
+ */
+typedef struct {
+  int32_t m_r;
+  int32_t n_r;
+  int32_t k_c;
+  int32_t m_c;
+  int32_t split_k;
+  int32_t dense_split_pct;
+  int32_t mode;
+} rosko_tile;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* rosko_status_string(rosko_status s);
+
+/*
+ * rosko_pack - Alg. 1 on the device, per row panel of m_r rows.
+ *
+ * A_dev   dense row-major M x K matrix of type a_dtype, leading dim lda >= K.
+ * a_dtype ROSKO_F32, ROSKO_BF16 or ROSKO_I8.
+ * packed_dtype  storage type of the nonzeros:
+ *           F32  from F32 (copy);   BF16 from F32 (round to nearest even) or BF16;
+ *           I8   from F32 (per-row symmetric scale s_i = max_k|a_ik|/127,
+ *                q = clamp(rint(a/s_i), -127, 127), mask = q != 0) or from I8
+ *                (row_scale_dev gives the scales, NULL = all 1);
+ *           F64  from F32 (exact widening; FP64 check mode).
+ * row_scale_dev  I8-from-I8 only: M FP32 row scales (device), else NULL.
+ * tile    only tile->m_r is read (NULL or m_r <= 0: library choice).
+ * out     receives the new handle (set to NULL on error).
+ * Zero test: IEEE a != 0, so -0.0 is dropped and NaN/Inf are kept.
+ * Synchronises `stream` once to size the packed buffers.  M or K may be 0.
+ */
+rosko_status rosko_pack(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64_t K,
+                        int64_t lda, rosko_dtype packed_dtype, const float* row_scale_dev,
+                        const rosko_tile* tile, rosko_stream_t stream, rosko_packed_t* out);
+
+/*
+ * rosko_spmm - C = A.B (accumulate = 0) or C += A.B (accumulate = 1, the
+ * in-place accumulation of Alg. 2, which loads C first).
+ *
+ * A       packed handle.  B_dev: K x N row-major of type b_dtype, leading dim
+ *         ldb >= N; B_dev and ldb * sizeof(b_dtype) must be 16-byte aligned
+ *         (B slabs are moved by TMA).  C_dev: M x N row-major, ldc >= N.
+ * Supported (packed, b_dtype -> c_dtype):
+ *         (F32, F32 -> F32), (BF16, BF16 -> F32), (I8, I8 -> I32),
+ *         (I8, I8 -> F32: C = s_i * t_j * sum q_a q_b with col_scale_dev = t),
+ *         (F64, F32 -> F64, check mode).
+ * col_scale_dev  N FP32 column scales of B for (I8, I8 -> F32), else NULL.
+ * tile    NULL = analytic rule; otherwise see rosko_tile.
+ * Accumulation: FP32 (FP64 in check mode, INT32 exact for I8) in registers.
+ * With split_k > 1 partial sums are added with atomics, so FP results may
+ * differ run to run in the last bits.  N may be 0 (no-op).
+ */
+rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                        int64_t ldb, const float* col_scale_dev, void* C_dev,
+                        rosko_dtype c_dtype, int64_t ldc, int accumulate,
+                        const rosko_tile* tile, rosko_stream_t stream);
+
+/* Release a packed handle and its device buffers.  NULL-safe. */
+void rosko_free(rosko_packed_t A);
+
+/*
+ * rosko_unpack - inverse of Alg. 1: writes the dense M x K matrix (packed
+ * dtype; I8 codes for I8) to A_dev_out with leading dim lda, zeros elsewhere.
+ */
+rosko_status rosko_unpack(rosko_packed_t A, void* A_dev_out, int64_t lda, rosko_stream_t stream);
+
+/*
+ * rosko_packed_info - sizes of a handle (any output pointer may be NULL):
+ * nnz, exact packed bytes (values + row indices + column records), number of
+ * B rows touched (distinct non-empty columns over all panels), number of
+ * panels, panel height m_r, packed dtype.  Synchronous (host data only,
+ * except touched_k which is computed at pack time).
+ */
+rosko_status rosko_packed_info(rosko_packed_t A, int64_t* nnz, int64_t* bytes,
+                               int64_t* touched_k, int64_t* n_panels, int32_t* m_r,
+                               int32_t* packed_dtype, int64_t* n_cols);
+
+/*
+ * rosko_packed_export - copy the canonical Alg. 1 arrays to host buffers,
+ * concatenated over panels in panel order (synchronous):
+ *   A_p_host   nnz values (packed dtype)       loc_m_host  nnz uint8 rows
+ *   col_ind_host  n_cols int32                 nnz_host    n_cols int32 counts
+ *   panel_cols_host  n_panels + 1 int64 offsets into col_ind / nnz
+ * Any pointer may be NULL to skip that array.
+ */
+rosko_status rosko_packed_export(rosko_packed_t A, void* A_p_host, uint8_t* loc_m_host,
+                                 int32_t* col_ind_host, int32_t* nnz_host,
+                                 int64_t* panel_cols_host);
+
+/*
+ * rosko_schedule_analytic - the closed-form tile rule (host only, no GPU
+ * needed): Eq. 1-3 of Sec. 4.2 re-derived for the GB300 register file,
+ * shared memory, L2 and 152 SMs.  Fills *tile for an M x K x N problem with
+ * nnz nonzeros whose packed panels have height m_r (<= 0: choose), values
+ * of type packed_dtype.
+ */
+rosko_status rosko_schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz,
+                                     int32_t m_r, rosko_dtype packed_dtype, rosko_tile* tile);
+
+/*
+ * rosko_device_status - read (and with clear != 0, reset) the current
+ * device's kernel error bits: 1 = bounded wait ran out, 2 = corrupt packed
+ * stream.  Synchronises the device.
+ */
+rosko_status rosko_device_status(int32_t* bits, int clear);
+
+/*
+ * rosko_kernel_launches - number of CUDA kernels this library has launched
+ * in the calling process since it was loaded (all devices, all streams).
+ * Host-only; used to count the library's launches inside a timed region.
+ */
+int64_t rosko_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROSKO_H_ */

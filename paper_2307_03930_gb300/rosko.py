@@ -1,0 +1,224 @@
+"""Thin ctypes binding of the C-ABI in include/rosko.h.
+
+Names match the C entry points; every function only marshals arguments
+(tensor -> device pointer, sizes, dtype codes, stream) and checks the returned
+status.  All compute happens in the CUDA library; if that library is missing
+this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libroskogb300.so")
+
+F32, BF16, I8, F64, I32 = 0, 1, 2, 3, 4
+SCHED_ANALYTIC, SCHED_AUTOTUNE, SCHED_LEARNED, SCHED_FORCED = 0, 1, 2, 3
+STATUS_NAMES = ["ROSKO_OK", "ROSKO_ERR_INVALID_ARG", "ROSKO_ERR_UNSUPPORTED", "ROSKO_ERR_OOM",
+                "ROSKO_ERR_CUDA", "ROSKO_ERR_TIMEOUT", "ROSKO_ERR_BAD_HANDLE", "ROSKO_ERR_DEVICE"]
+TORCH_TO_CODE = {torch.float32: F32, torch.bfloat16: BF16, torch.int8: I8,
+                 torch.float64: F64, torch.int32: I32}
+CODE_TO_TORCH = {v: k for k, v in TORCH_TO_CODE.items()}
+ELEM_SIZE = {F32: 4, BF16: 2, I8: 1, F64: 8, I32: 4}
+
+
+class RoskoError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else f"status {status}"
+        super().__init__(f"{what} failed: {name}")
+
+
+class rosko_tile(ctypes.Structure):
+    _fields_ = [("m_r", ctypes.c_int32), ("n_r", ctypes.c_int32), ("k_c", ctypes.c_int32),
+                ("m_c", ctypes.c_int32), ("split_k", ctypes.c_int32),
+                ("dense_split_pct", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def make_tile(**kw) -> rosko_tile:
+    t = rosko_tile()
+    for f, _ in rosko_tile._fields_:
+        setattr(t, f, int(kw.get(f, 0)))
+    return t
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run `python -m paper_2307_03930_gb300.build`)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+    P_tile = ctypes.POINTER(rosko_tile)
+    sig = {
+        "rosko_status_string": (ctypes.c_char_p, [ci]),
+        "rosko_pack": (ci, [vp, ci, i64, i64, i64, ci, vp, P_tile, vp, ctypes.POINTER(vp)]),
+        "rosko_spmm": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, ci, P_tile, vp]),
+        "rosko_free": (None, [vp]),
+        "rosko_unpack": (ci, [vp, vp, i64, vp]),
+        "rosko_packed_info": (ci, [vp] + [ctypes.POINTER(i64)] * 4 +
+                              [ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]),
+        "rosko_packed_export": (ci, [vp, vp, vp, vp, vp, vp]),
+        "rosko_schedule_analytic": (ci, [i64, i64, i64, i64, i32, ci, P_tile]),
+        "rosko_device_status": (ci, [ctypes.POINTER(i32), ci]),
+        "rosko_kernel_launches": (i64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise RoskoError(status, what)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected (the library works on device pointers)")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("row-major 2-D tensor with unit column stride expected")
+    return int(t.stride(0))
+
+
+class PackedA:
+    """Owner of a rosko_packed_t handle; frees it when collected."""
+
+    def __init__(self, handle: int, M: int, K: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.M, self.K = M, K
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.rosko_free(h)
+            self.handle = None
+
+    def free(self):
+        rosko_free(self)
+
+    def info(self) -> dict:
+        return rosko_packed_info(self)
+
+
+def rosko_status_string(status: int) -> str:
+    return lib().rosko_status_string(int(status)).decode()
+
+
+def rosko_pack(A: torch.Tensor, packed_dtype: int, m_r: int = 0,
+               row_scale: Optional[torch.Tensor] = None, stream=None) -> PackedA:
+    """Alg. 1 on the device: pack the dense row-major A (F32, BF16 or I8)."""
+    L = lib()
+    M, K = A.shape
+    lda = _ld(A) if A.numel() else max(K, 1)
+    tile = make_tile(m_r=m_r)
+    out = ctypes.c_void_p()
+    st = L.rosko_pack(_ptr(A) if A.numel() else None, TORCH_TO_CODE[A.dtype], M, K, lda,
+                      int(packed_dtype), _ptr(row_scale), ctypes.byref(tile),
+                      ctypes.c_void_p(_stream(stream)), ctypes.byref(out))
+    _check(st, "rosko_pack")
+    return PackedA(out.value, M, K)
+
+
+def rosko_spmm(A: PackedA, B: torch.Tensor, C: torch.Tensor,
+               col_scale: Optional[torch.Tensor] = None, accumulate: bool = False,
+               tile: Optional[rosko_tile] = None, stream=None) -> torch.Tensor:
+    """C = A.B (or C += A.B); returns C."""
+    L = lib()
+    K, N = B.shape
+    st = L.rosko_spmm(A.handle, _ptr(B) if B.numel() else None, TORCH_TO_CODE[B.dtype], N,
+                      _ld(B) if B.numel() else max(N, 1), _ptr(col_scale),
+                      _ptr(C) if C.numel() else None, TORCH_TO_CODE[C.dtype],
+                      _ld(C) if C.numel() else max(N, 1), int(bool(accumulate)),
+                      ctypes.byref(tile) if tile is not None else None,
+                      ctypes.c_void_p(_stream(stream)))
+    _check(st, "rosko_spmm")
+    return C
+
+
+def rosko_free(A: PackedA) -> None:
+    if A.handle is not None and A.handle.value:
+        lib().rosko_free(A.handle)
+    A.handle = None
+
+
+def rosko_unpack(A: PackedA, out: torch.Tensor, stream=None) -> torch.Tensor:
+    st = lib().rosko_unpack(A.handle, _ptr(out), _ld(out), ctypes.c_void_p(_stream(stream)))
+    _check(st, "rosko_unpack")
+    return out
+
+
+def rosko_packed_info(A: PackedA) -> dict:
+    i64 = [ctypes.c_int64() for _ in range(5)]
+    m_r, dt = ctypes.c_int32(), ctypes.c_int32()
+    st = lib().rosko_packed_info(A.handle, ctypes.byref(i64[0]), ctypes.byref(i64[1]),
+                                 ctypes.byref(i64[2]), ctypes.byref(i64[3]),
+                                 ctypes.byref(m_r), ctypes.byref(dt), ctypes.byref(i64[4]))
+    _check(st, "rosko_packed_info")
+    return {"nnz": i64[0].value, "bytes": i64[1].value, "touched_k": i64[2].value,
+            "n_panels": i64[3].value, "m_r": m_r.value, "dtype": dt.value,
+            "n_cols": i64[4].value}
+
+
+def rosko_packed_export(A: PackedA) -> dict:
+    """Canonical Alg. 1 arrays (numpy), concatenated over panels."""
+    import numpy as np
+    info = rosko_packed_info(A)
+    np_dt = {F32: np.float32, BF16: np.uint16, I8: np.int8, F64: np.float64}[info["dtype"]]
+    A_p = np.zeros(info["nnz"], dtype=np_dt)
+    loc_m = np.zeros(info["nnz"], dtype=np.uint8)
+    col_ind = np.zeros(info["n_cols"], dtype=np.int32)
+    nnz = np.zeros(info["n_cols"], dtype=np.int32)
+    panel_cols = np.zeros(info["n_panels"] + 1, dtype=np.int64)
+    c = lambda a: ctypes.c_void_p(a.ctypes.data) if a.size else None
+    st = lib().rosko_packed_export(A.handle, c(A_p), c(loc_m), c(col_ind), c(nnz), c(panel_cols))
+    _check(st, "rosko_packed_export")
+    return {"A_p": A_p, "loc_m": loc_m, "col_ind": col_ind, "nnz": nnz, "panel_cols": panel_cols}
+
+
+def rosko_schedule_analytic(M: int, K: int, N: int, nnz: int, m_r: int = 0,
+                            packed_dtype: int = F32) -> dict:
+    t = rosko_tile()
+    _check(lib().rosko_schedule_analytic(M, K, N, nnz, m_r, packed_dtype, ctypes.byref(t)),
+           "rosko_schedule_analytic")
+    return t.as_dict()
+
+
+def rosko_device_status(clear: bool = False) -> int:
+    v = ctypes.c_int32()
+    _check(lib().rosko_device_status(ctypes.byref(v), int(bool(clear))), "rosko_device_status")
+    return v.value
+
+
+def rosko_kernel_launches() -> int:
+    return int(lib().rosko_kernel_launches())

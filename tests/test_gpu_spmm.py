@@ -1,0 +1,194 @@
+"""Sparse SpMM (Alg. 2 on CUDA cores) against the FP64/int64 oracle.  GPU only.
+
+Bars: INT8 -> INT32 bit-exact; FP32 and BF16-in/FP32-accumulate within 1e-5
+of the normalised error max|C - C_ref| / sum_k |a||b| (BF16 against the oracle
+on the BF16-rounded inputs; within 1e-2 against the unrounded inputs); FP64
+check mode within 1e-13."""
+import numpy as np
+import pytest
+import torch
+
+from tests._lib import built
+from oracle.spmm import spmm, spmm_int, normalized_error
+from oracle.quant import bf16_round, quantize_rows_int8, quantize_cols_int8
+from paper_2307_03930_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-5, "bf16": 1e-5, "f64": 1e-13, "i8f": 1e-5}
+
+
+def _problem(M, K, N, s, seed, pattern="uniform", relu_b=False):
+    rng = gen.rng_for(seed, M, K, N)
+    A = gen.sparse_weight(M, K, s, rng, pattern)
+    B = gen.relu_normal((K, N), rng) if relu_b else gen.normal((K, N), rng)
+    return A, B
+
+
+def _ldpad(X, elem):
+    """Device copy of X with a leading dimension rounded up to 16 bytes."""
+    K, N = X.shape
+    per = 16 // elem
+    ld = max(per, -(-N // per) * per)
+    buf = torch.zeros((K, ld), dtype=X.dtype, device="cuda")
+    buf[:, :N] = X.cuda()
+    return buf[:, :N]
+
+
+def run(rosko, A, B, mode, m_r=32, tile=None, accumulate=False, C0=None, rows=None):
+    """Run the library on (A, B) in `mode` and return (C_gpu[rows], C_ref, D)."""
+    M, K = A.shape
+    N = B.shape[1]
+    if mode == "f32":
+        h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.F32, m_r=m_r)
+        Bd = _ldpad(torch.from_numpy(B), 4)
+        C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+        Ar, Br = A, B
+    elif mode == "bf16":
+        h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16, m_r=m_r)
+        Bd = _ldpad(torch.from_numpy(B).to(torch.bfloat16), 2)
+        C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+        Ar, Br = bf16_round(A), bf16_round(B)
+    elif mode == "f64":
+        h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.F64, m_r=m_r)
+        Bd = _ldpad(torch.from_numpy(B), 4)
+        C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+        Ar, Br = A, B
+    elif mode in ("i8", "i8f"):
+        qa, sa = quantize_rows_int8(A)
+        qb, sb = quantize_cols_int8(B)
+        h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.I8, m_r=m_r)
+        Bd = _ldpad(torch.from_numpy(qb), 1)
+        C = torch.zeros((M, N), dtype=torch.int32 if mode == "i8" else torch.float32,
+                        device="cuda")
+    if C0 is not None:
+        C.copy_(torch.from_numpy(C0).to(C.dtype))
+    col_scale = torch.from_numpy(sb).cuda() if mode == "i8f" else None
+    rosko.rosko_spmm(h, Bd, C, col_scale=col_scale, accumulate=accumulate, tile=tile)
+    torch.cuda.synchronize()
+    assert rosko.rosko_device_status(clear=True) == 0
+    Cg = C.cpu().numpy()
+    rows = np.arange(M) if rows is None else np.asarray(rows)
+    Cg = Cg[rows]
+    if mode == "i8":
+        ref = spmm_int(qa, qb, rows=rows, C0=C0.astype(np.int64) if C0 is not None else None)
+        return Cg, ref, None
+    if mode == "i8f":
+        ci = spmm_int(qa, qb, rows=rows).astype(np.float64)
+        ref = ci * sa[rows, None].astype(np.float64) * sb[None, :].astype(np.float64)
+        D = np.abs(qa[rows]).astype(np.float64) @ np.abs(qb).astype(np.float64)
+        D = D * sa[rows, None] * sb[None, :]
+        if C0 is not None:
+            ref = ref + C0[rows]
+            D = D + np.abs(C0[rows])
+        return Cg, ref, D
+    ref, D = spmm(Ar, Br, rows=rows, C0=C0)
+    if C0 is not None:
+        D = D + np.abs(C0[rows].astype(np.float64))
+    return Cg, ref, D
+
+
+def check(mode, Cg, ref, D):
+    if mode == "i8":
+        assert np.array_equal(Cg.astype(np.int64), ref)
+        return 0.0
+    err = normalized_error(Cg, ref, D)
+    assert err <= TOL[mode], err
+    return err
+
+
+SHAPES = [(1, 1, 1, 0.0), (33, 17, 65, 0.5), (70, 300, 129, 0.9), (200, 1000, 300, 0.99),
+          (64, 96, 40, 1.0), (130, 77, 257, 0.0)]
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16", "i8", "i8f", "f64"])
+@pytest.mark.parametrize("M,K,N,s", SHAPES)
+def test_small_ragged(mode, M, K, N, s):
+    rosko = built()
+    A, B = _problem(M, K, N, s, seed=0)
+    m_r = 16 if mode == "f64" else 32
+    check(mode, *run(rosko, A, B, mode, m_r=m_r))
+
+
+# every compiled (m_r, V) variant with several CTA heights, slabs and K splits
+VARIANTS = {"f32": [(32, 4), (16, 8), (16, 4), (8, 8)], "bf16": [(32, 4), (16, 8), (8, 8)],
+            "i8": [(32, 4), (16, 8), (8, 8)], "i8f": [(32, 4), (16, 8), (8, 8)],
+            "f64": [(32, 2), (16, 4), (8, 4)]}
+
+
+@pytest.mark.parametrize("mode", list(VARIANTS))
+@pytest.mark.parametrize("W,KC,split", [(1, 8, 1), (3, 32, 3), (8, 64, 2), (4, 256, 1)])
+def test_forced_tiles(mode, W, KC, split):
+    rosko = built()
+    A, B = _problem(150, 700, 300, 0.8, seed=1)
+    esz = {"f32": 4, "bf16": 2, "i8": 1, "i8f": 1, "f64": 4}[mode]
+    for R, V in VARIANTS[mode]:
+        t = rosko.make_tile(m_r=R, n_r=32 * V, k_c=KC, m_c=W * R, split_k=split,
+                            mode=rosko.SCHED_FORCED)
+        if 2 * KC * 32 * V * esz > 200 * 1024:
+            # a two-slab ring would not fit in shared memory: rejected on the host
+            with pytest.raises(rosko.RoskoError) as ei:
+                run(rosko, A, B, mode, m_r=R, tile=t)
+            assert ei.value.status == 1
+            continue
+        check(mode, *run(rosko, A, B, mode, m_r=R, tile=t))
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16", "i8", "i8f", "f64"])
+@pytest.mark.parametrize("split", [1, 4])
+def test_accumulate_in_place(mode, split):
+    # Alg. 2 loads C first: C += A.B
+    rosko = built()
+    A, B = _problem(90, 500, 200, 0.9, seed=2)
+    rng = np.random.default_rng(5)
+    if mode == "i8":
+        C0 = rng.integers(-1000, 1000, size=(90, 200)).astype(np.int32)
+    else:
+        C0 = rng.standard_normal((90, 200)).astype(np.float64 if mode == "f64" else np.float32)
+    m_r = 16 if mode == "f64" else 32
+    t = rosko.make_tile(split_k=split)
+    check(mode, *run(rosko, A, B, mode, m_r=m_r, tile=t, accumulate=True, C0=C0))
+
+
+def test_identity_and_zero():
+    rosko = built()
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((64, 100)).astype(np.float32)
+    Cg, ref, D = run(rosko, np.eye(64, dtype=np.float32), B, "f32")
+    assert np.array_equal(Cg, B)
+    Cg, ref, D = run(rosko, np.zeros((64, 64), np.float32), B, "f32")
+    assert np.all(Cg == 0)
+    Bb = bf16_round(B)
+    Cg, _, _ = run(rosko, np.eye(64, dtype=np.float32), Bb, "bf16")
+    assert np.array_equal(Cg, Bb)
+
+
+def test_bf16_against_unrounded_inputs():
+    rosko = built()
+    A, B = _problem(256, 2048, 512, 0.9, seed=3, pattern="magnitude", relu_b=True)
+    Cg, ref, D = run(rosko, A, B, "bf16")
+    assert normalized_error(Cg, ref, D) <= 1e-5
+    ref_u, D_u = spmm(A, B)
+    assert normalized_error(Cg, ref_u, D_u) <= 1e-2
+
+
+def test_c1_full_size_fp32():
+    # 1024 x 1024 at 90% uniform sparsity times a 1024 x 1024 N(0,1) B, seed 0
+    rosko = built()
+    rng = gen.rng_for(0)
+    A = gen.sparse_weight(1024, 1024, 0.9, rng, "uniform")
+    B = gen.normal((1024, 1024), rng)
+    check("f32", *run(rosko, A, B, "f32"))
+
+
+@pytest.mark.parametrize("s", [0.5, 0.7, 0.9, 0.95, 0.99, 0.998])
+@pytest.mark.parametrize("mode", ["f32", "bf16"])
+def test_c2_full_size_sampled(s, mode):
+    # conv-layer shape: A 512 x 4608 magnitude-pruned, B 4608 x 3136 post-ReLU,
+    # seed 1; the analytic schedule the bench uses; 48 sampled rows vs oracle
+    rosko = built()
+    rng = gen.rng_for(1, int(round(s * 1000)))
+    A = gen.magnitude_prune(gen.normal((512, 4608), rng), s)
+    B = gen.relu_normal((4608, 3136), rng)
+    rows = np.random.default_rng(int(s * 1000)).choice(512, 48, replace=False)
+    check(mode, *run(rosko, A, B, mode, rows=rows))

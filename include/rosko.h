@@ -76,10 +76,26 @@ typedef enum {
  *   k_c   rows of B staged in shared memory per pipeline slab.
  *   m_c   C rows per CTA = warps per CTA x m_r.
  *   split_k  number of K ranges reduced into C with atomics (>= 1).
- *   dense_split_pct  tensor-core dense-panel path for panels whose density
- *         in percent is >= this value; 101 = never.
+ *   dense_split_pct  BF16 only: 128-row tiles of A whose density in percent
+ *         is >= this value run on the tensor-core dense-panel path, the
+ *         others on the sparse path; >= 101 = never.  At pack time the same
+ *         field is the minimum density for which a dense copy is kept.
+ *   dense_n_r      C columns per tensor-core CTA tile (128 or 256).
+ *   dense_split_k  CTAs over which the stream-K tensor-core path divides its
+ *         (tile, K slab) work (default: one per SM); a tile whose K range
+ *         is divided is added into C with atomics.
+ *   order traversal of a panel inside a B slab by the CUDA-core path:
+ *         1 = column order, Alg. 2 as printed (one B row per packed column,
+ *         the C row picked by a run-time switch over loc_m);
+ *         2 = row-slot order (each register row of C walks its own
+ *         nonzeros and reads their B rows from the shared slab; needs
+ *         K < 65280);
+ *         3 = row-slot order over a gather of only the B rows the CTA's
+ *         128-row tile touches (the tile's col_ind); needs m_r = 16,
+ *         m_c = 128.
  *   mode  a rosko_sched_mode.
- * A field <= 0 means "library chooses" (except in ROSKO_SCHED_FORCED).
+ * A field <= 0 means "library chooses" (except in ROSKO_SCHED_FORCED, where
+ * the sparse fields must be set and dense fields <= 0 still mean default).
  */
 typedef struct {
   int32_t m_r;
@@ -88,6 +104,9 @@ typedef struct {
   int32_t m_c;
   int32_t split_k;
   int32_t dense_split_pct;
+  int32_t dense_n_r;
+  int32_t dense_split_k;
+  int32_t order;
   int32_t mode;
 } rosko_tile;
 
@@ -106,7 +125,9 @@ const char* rosko_status_string(rosko_status s);
  *                (row_scale_dev gives the scales, NULL = all 1);
  *           F64  from F32 (exact widening; FP64 check mode).
  * row_scale_dev  I8-from-I8 only: M FP32 row scales (device), else NULL.
- * tile    only tile->m_r is read (NULL or m_r <= 0: library choice).
+ * tile    only tile->m_r and, for BF16, tile->dense_split_pct (minimum tile
+ *         density, in percent, for keeping a dense copy; <= 0: 1%) are read.
+ *         m_r <= 0: 16.
  * out     receives the new handle (set to NULL on error).
  * Zero test: IEEE a != 0, so -0.0 is dropped and NaN/Inf are kept.
  * Synchronises `stream` once to size the packed buffers.  M or K may be 0.
@@ -131,6 +152,8 @@ rosko_status rosko_pack(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64
  * Accumulation: FP32 (FP64 in check mode, INT32 exact for I8) in registers.
  * With split_k > 1 partial sums are added with atomics, so FP results may
  * differ run to run in the last bits.  N may be 0 (no-op).
+ * Dense-panel tiles (BF16) multiply their explicit zeros too, so there a
+ * non-finite B value meets 0 * Inf = NaN, while skipped rows never see it.
  */
 rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
                         int64_t ldb, const float* col_scale_dev, void* C_dev,
@@ -148,7 +171,8 @@ rosko_status rosko_unpack(rosko_packed_t A, void* A_dev_out, int64_t lda, rosko_
 
 /*
  * rosko_packed_info - sizes of a handle (any output pointer may be NULL):
- * nnz, exact packed bytes (values + row indices + column records), number of
+ * nnz, exact bytes of the device format the SpMM reads (nonzero records,
+ * column records, panel offsets), number of
  * B rows touched (distinct non-empty columns over all panels), number of
  * panels, panel height m_r, packed dtype.  Synchronous (host data only,
  * except touched_k which is computed at pack time).
@@ -178,6 +202,33 @@ rosko_status rosko_packed_export(rosko_packed_t A, void* A_p_host, uint8_t* loc_
  */
 rosko_status rosko_schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz,
                                      int32_t m_r, rosko_dtype packed_dtype, rosko_tile* tile);
+
+/*
+ * rosko_num_candidates - size of the fixed candidate schedule set searched by
+ * the autotuner and predicted by the learned selector (host only).
+ */
+int32_t rosko_num_candidates(void);
+
+/*
+ * rosko_candidate - candidate schedule `index` for handle A and width N, as a
+ * ROSKO_SCHED_FORCED tile.  Returns ROSKO_ERR_UNSUPPORTED when the candidate
+ * does not apply to this handle (e.g. a dense split on a non-BF16 pack).
+ */
+rosko_status rosko_candidate(rosko_packed_t A, int64_t N, int32_t index, rosko_tile* out);
+
+/*
+ * rosko_autotune - per-shape search (Sec. 6: the tile parameters are exposed
+ * for auto-tuning).  Times every applicable candidate on (A, B, C) with CUDA
+ * events on `stream` (one untimed launch, then `reps` timed launches), writes
+ * the fastest to *best and caches it for (A, N): a later rosko_spmm with
+ * tile->mode = ROSKO_SCHED_AUTOTUNE uses it.  C is used as scratch output.
+ * times_ms (optional, rosko_num_candidates() floats) receives each
+ * candidate's mean time in ms, -1 where it does not apply.  Synchronises.
+ */
+rosko_status rosko_autotune(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                            int64_t ldb, const float* col_scale_dev, void* C_dev,
+                            rosko_dtype c_dtype, int64_t ldc, int32_t reps, rosko_tile* best,
+                            float* times_ms, rosko_stream_t stream);
 
 /*
  * rosko_device_status - read (and with clear != 0, reset) the current

@@ -37,14 +37,14 @@ def spmm(A, B, rows=None, cols=None, C0=None):
     cols = _index(cols, B.shape[1])
     C = np.zeros((rows.size, cols.size), dtype=np.float64)
     D = np.zeros_like(C)
-    Bc = B[:, cols].astype(np.float64)
     for out_i, i in enumerate(rows):
         acc = C[out_i]
         nrm = D[out_i]
         for k in np.flatnonzero(A[i] != 0):     # k ascending, zeros skipped
             a = np.float64(A[i, k])
-            acc += a * Bc[k]
-            nrm += abs(a) * np.abs(Bc[k])
+            b = B[k, cols].astype(np.float64)
+            acc += a * b
+            nrm += abs(a) * np.abs(b)
     if C0 is not None:
         C += np.asarray(C0, dtype=np.float64)[np.ix_(rows, cols)]
     return C, D
@@ -59,11 +59,10 @@ def spmm_int(Aq, Bq, rows=None, cols=None, C0=None):
     rows = _index(rows, M)
     cols = _index(cols, Bq.shape[1])
     C = np.zeros((rows.size, cols.size), dtype=np.int64)
-    Bc = Bq[:, cols].astype(np.int64)
     for out_i, i in enumerate(rows):
         acc = C[out_i]
         for k in np.flatnonzero(Aq[i] != 0):
-            acc += np.int64(Aq[i, k]) * Bc[k]
+            acc += np.int64(Aq[i, k]) * Bq[k, cols].astype(np.int64)
     if C0 is not None:
         C += np.asarray(C0, dtype=np.int64)[np.ix_(rows, cols)]
     lim = np.int64(2 ** 31)

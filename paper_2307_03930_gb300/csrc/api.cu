@@ -111,19 +111,62 @@ CUresult encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank,
 // ceil(M / m_c) times, so m_c = W m_r grows with M; K is split only as far as
 // needed to put ~2 CTAs on every SM.
 // ---------------------------------------------------------------------------
+// Tensor-core dense-panel tiles: the stream-K kernel spreads the work over one
+// CTA per SM whatever the tile count, so only the CTA width matters: 256 halves
+// the L2->SM traffic of A (read once per column tile) against 128.
+void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, int* ctas_out) {
+  (void)n_tiles;
+  (void)K;
+  *TN_out = N > 128 ? 256 : 128;
+  *ctas_out = sms;
+}
+
+// Density (in percent) from which a 128-row tile runs on the tensor cores.
+// Sec. 4.2 balances work against bandwidth; here the balance is between two
+// engines: a dense tile costs 2*128*K*N tensor-core flops, its sparse form
+// 2*nnz*N CUDA-core flops.  With ~1.6 PFLOP/s (BF16 dense, measured) against
+// an effective ~35 TFLOP/s for the row-skipping kernel the break-even density
+// is ~2%; 3% leaves margin for the tensor path's B reads at high sparsity.
+constexpr int kDenseSplitPct = 3;
+constexpr int kDenseCopyPct = 1;
+
+// ---------------------------------------------------------------------------
+// Analytic schedule: Sec. 4.2 re-derived for one GB300.
+//
+// Register level (Eq. 3 analog): a warp keeps an m_r x 32V C tile in
+// registers; each staged B element is reused d*m_r times, so m_r is as large
+// as the register file allows (m_r * V accumulators <= 128 per lane).
+// Shared-memory level (Eq. 1 analog, per SM instead of per core): the ring of
+// `stages` k_c x n_r B slabs must leave room for two CTAs per SM
+// (<= ~100 KB each) so that one CTA's epilogue overlaps another's stream.
+// Chip level (Eq. 2 analog): B is re-read from L2 once per CTA row group,
+// ceil(M / m_c) times, so m_c = W m_r grows with M; K is split only as far as
+// needed to put ~2 CTAs on every SM.
+// ---------------------------------------------------------------------------
 rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int32_t m_r,
                                rosko_dtype dt, int sms, rosko_tile* t) {
-  (void)nnz;
-  if (m_r <= 0) m_r = (dt == ROSKO_F64) ? 16 : 32;
-  const int V = sparse_default_V(dt, m_r);
+  if (m_r <= 0) m_r = 16;
+  const double d = (M * K > 0) ? (double)nnz / ((double)M * (double)K) : 0.0;
+  // Traversal: row-slot (no run-time register indexing, needs 16-bit k).
+  // Below ~5% density a 128-row tile leaves many B rows untouched
+  // ((1-d)^128 of them), so the tile gathers only the rows its panels touch.
+  int order = K < kRowSlotMaxK ? 2 : 1;
+  if (order == 2 && m_r == 16 && d < 0.05) order = 3;
+  const int V = sparse_default_V(dt, m_r, order);
   const int NR = 32 * V;
   const int64_t P = (M + m_r - 1) / m_r;
   int W = 4;
   if (P >= 64) W = 8;
   if (P < 4) W = (int)std::max<int64_t>(P, 1);
-  const int KC = 32;
+  if (order == 3) W = 128 / m_r;  // one CTA per 128-row tile
+  // 4-slab ring within ~100 KB so two CTAs share an SM
+  const int64_t bsz = (dt == ROSKO_BF16) ? 2 : (dt == ROSKO_I8 ? 1 : 4);
+  int KC = (int)((100 * 1024) / (4 * (int64_t)NR * bsz)) / 8 * 8;
+  KC = std::max(8, std::min(64, KC));
   const int64_t tiles = ((P + W - 1) / W) * ((N + NR - 1) / NR);
-  const int64_t slabs = (K + KC - 1) / KC;
+  // order 3 streams only the touched rows of each tile: ~(1 - (1-d)^128) K
+  const double touched = order == 3 ? 1.0 - std::pow(1.0 - d, 128.0) : 1.0;
+  const int64_t slabs = std::max<int64_t>(1, (int64_t)((double)K * touched) / KC);
   int64_t split = 1;
   const int64_t target = 2LL * sms;
   if (tiles > 0 && tiles < target) split = (target + tiles - 1) / tiles;
@@ -133,7 +176,12 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
   t->k_c = KC;
   t->m_c = W * m_r;
   t->split_k = (int32_t)split;
-  t->dense_split_pct = 101;
+  t->dense_split_pct = (dt == ROSKO_BF16) ? kDenseSplitPct : 101;
+  int TN = 256, ds = 1;
+  dense_config((M + 127) / 128, N, K, sms, &TN, &ds);
+  t->dense_n_r = TN;
+  t->dense_split_k = ds;
+  t->order = order;
   t->mode = ROSKO_SCHED_ANALYTIC;
   return ROSKO_OK;
 }
@@ -176,13 +224,21 @@ rosko_status rosko_pack(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64
   if (!ok_pair) return ROSKO_ERR_UNSUPPORTED;
   if (row_scale_dev && !(a_dtype == ROSKO_I8 && packed_dtype == ROSKO_I8))
     return ROSKO_ERR_INVALID_ARG;
-  int32_t m_r = (tile && tile->m_r > 0) ? tile->m_r : (packed_dtype == ROSKO_F64 ? 16 : 32);
-  if (m_r != 8 && m_r != 16 && m_r != 32) return ROSKO_ERR_INVALID_ARG;
+  int32_t m_r = (tile && tile->m_r > 0) ? tile->m_r : 0;
+  if (m_r != 0 && m_r != 8 && m_r != 16 && m_r != 32) return ROSKO_ERR_INVALID_ARG;
+  if (m_r == 0) {
+    // Eq. 3 analog: a warp holds m_r rows of C; 16 rows per panel make eight
+    // panels per 128-row tile (the unit of the dense split and of the
+    // touched-row gather) while leaving registers for wide column strips.
+    m_r = 16;
+  }
   const int64_t P = (M + m_r - 1) / m_r;
   if (P > 65535) return ROSKO_ERR_INVALID_ARG;
+  const int32_t dense_min = (tile && tile->dense_split_pct > 0) ? tile->dense_split_pct
+                                                                 : kDenseCopyPct;
   rosko_packed_s* h = nullptr;
   rosko_status s = pack_impl(A_dev, a_dtype, M, K, lda, packed_dtype, row_scale_dev, m_r,
-                             static_cast<cudaStream_t>(stream), &h);
+                             dense_min, static_cast<cudaStream_t>(stream), &h);
   if (s != ROSKO_OK) return s;
   *out = h;
   return ROSKO_OK;
@@ -193,6 +249,9 @@ void rosko_free(rosko_packed_t A) {
   A->magic = 0;
   if (A->meta_base) cudaFree(A->meta_base);
   if (A->data_base) cudaFree(A->data_base);
+  if (A->dense_base) cudaFree(A->dense_base);
+  if (A->row_base) cudaFree(A->row_base);
+  if (A->gather_base) cudaFree(A->gather_base);
   delete A;
 }
 
@@ -204,10 +263,16 @@ rosko_status rosko_schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nn
   return schedule_analytic(M, K, N, nnz, m_r, packed_dtype, 152, tile);
 }
 
-rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
-                        int64_t ldb, const float* col_scale_dev, void* C_dev,
-                        rosko_dtype c_dtype, int64_t ldc, int accumulate,
-                        const rosko_tile* tile, rosko_stream_t stream) {
+}  // extern "C"
+
+namespace rosko {
+// Host-side checks shared by every SpMM entry point.  *done is set when the
+// call is complete without a launch (empty shapes, all-zero A).
+rosko_status spmm_validate(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                           int64_t ldb, const float* col_scale_dev, void* C_dev,
+                           rosko_dtype c_dtype, int64_t ldc, int accumulate, cudaStream_t st,
+                           bool* done) {
+  *done = false;
   if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
   if (!dtype_valid(b_dtype) || !dtype_valid(c_dtype)) return ROSKO_ERR_INVALID_ARG;
   if (N < 0 || ldb < std::max<int64_t>(N, 1) || ldc < std::max<int64_t>(N, 1))
@@ -222,14 +287,17 @@ rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype
   if (!combo) return ROSKO_ERR_UNSUPPORTED;
   const bool dequant = (p == ROSKO_I8 && c_dtype == ROSKO_F32);
   if (dequant != (col_scale_dev != nullptr)) return ROSKO_ERR_INVALID_ARG;
-  if (A->M == 0 || N == 0) return ROSKO_OK;
+  if (A->M == 0 || N == 0) {
+    *done = true;
+    return ROSKO_OK;
+  }
   if (!C_dev) return ROSKO_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ROSKO_ERR_CUDA;
   if (dev != A->device) return ROSKO_ERR_INVALID_ARG;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t csz = dtype_size(c_dtype);
   if (A->K == 0 || A->nnz == 0) {
+    *done = true;
     if (accumulate) return ROSKO_OK;
     return cudaMemset2DAsync(C_dev, (size_t)ldc * csz, 0, (size_t)N * csz, (size_t)A->M, st) ==
                    cudaSuccess
@@ -240,37 +308,182 @@ rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype
   const size_t bsz = dtype_size(b_dtype);
   if ((reinterpret_cast<uintptr_t>(B_dev) % 16) != 0 || ((size_t)ldb * bsz) % 16 != 0)
     return ROSKO_ERR_INVALID_ARG;
+  return ROSKO_OK;
+}
 
+// Resolve the tile (fields <= 0 take the analytic rule) and launch the dense
+// and sparse paths.  Arguments were validated by spmm_validate.
+rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                      int64_t ldb, const float* col_scale_dev, void* C_dev, rosko_dtype c_dtype,
+                      int64_t ldc, int accumulate, const rosko_tile* tile, cudaStream_t st) {
+  const rosko_dtype p = A->dt;
+  const size_t bsz = dtype_size(b_dtype);
+  const size_t csz = dtype_size(c_dtype);
   rosko_tile t{};
   const bool forced = tile && tile->mode == ROSKO_SCHED_FORCED;
-  schedule_analytic(A->M, A->K, N, A->nnz, A->m_r, p, num_sms(), &t);
+  const int sms = num_sms();
+  schedule_analytic(A->M, A->K, N, A->nnz, A->m_r, p, sms, &t);
   if (tile) {
     if (tile->m_r > 0 && tile->m_r != A->m_r) return ROSKO_ERR_INVALID_ARG;
+    if (forced && (tile->n_r <= 0 || tile->k_c <= 0 || tile->m_c <= 0 || tile->split_k <= 0))
+      return ROSKO_ERR_INVALID_ARG;
     if (tile->n_r > 0) t.n_r = tile->n_r;
     if (tile->k_c > 0) t.k_c = tile->k_c;
     if (tile->m_c > 0) t.m_c = tile->m_c;
     if (tile->split_k > 0) t.split_k = tile->split_k;
-    if (forced && (tile->n_r <= 0 || tile->k_c <= 0 || tile->m_c <= 0 || tile->split_k <= 0))
-      return ROSKO_ERR_INVALID_ARG;
+    if (tile->dense_split_pct > 0) t.dense_split_pct = tile->dense_split_pct;
+    if (tile->dense_n_r > 0) t.dense_n_r = tile->dense_n_r;
+    if (tile->dense_split_k > 0) t.dense_split_k = tile->dense_split_k;
+    if (tile->order > 0) t.order = tile->order;
   }
+  // ---- dense-panel split: a prefix of the density-sorted dense copies ----
+  int64_t n_dense = 0, dense_panels = 0;
+  if (p == ROSKO_BF16 && A->n_copy > 0 && t.dense_split_pct <= 100) {
+    while (n_dense < A->n_copy &&
+           A->tile_density[(size_t)n_dense] * 100.0 >= (double)t.dense_split_pct) {
+      dense_panels += A->tile_panels[(size_t)A->tile_order[(size_t)n_dense]];
+      ++n_dense;
+    }
+  }
+  if (n_dense > 0) {
+    if (t.dense_n_r != 128 && t.dense_n_r != 256) return ROSKO_ERR_INVALID_ARG;
+    if (t.dense_split_k < 1 || t.dense_split_k > 65535) return ROSKO_ERR_INVALID_ARG;
+    if (!tile || tile->dense_n_r <= 0 || tile->dense_split_k <= 0) {
+      int TN = 256, ds = 1;
+      dense_config(n_dense, N, A->K, sms, &TN, &ds);
+      if (!tile || tile->dense_n_r <= 0) t.dense_n_r = TN;
+      if (!tile || tile->dense_split_k <= 0) t.dense_split_k = ds;
+    }
+  }
+  const int64_t n_sparse = A->P - dense_panels;
+
   SparseLaunch L;
   L.R = A->m_r;
+  if (tile && tile->order > 0 && tile->n_r <= 0) {
+    // order forced without a width: the default width of that order
+    t.n_r = 32 * sparse_default_V(p, A->m_r, tile->order);
+  }
   if (t.n_r % 32 != 0) return ROSKO_ERR_INVALID_ARG;
   L.V = t.n_r / 32;
   if (t.m_c % A->m_r != 0) return ROSKO_ERR_INVALID_ARG;
   L.W = t.m_c / A->m_r;
   L.KC = t.k_c;
   L.split = t.split_k;
+  L.order = t.order;
+  if (L.order < 1 || L.order > 3) return ROSKO_ERR_INVALID_ARG;
+  if (L.order == 3 && (!A->gnz || A->m_r != 16)) {
+    if (tile && tile->order == 3) return ROSKO_ERR_UNSUPPORTED;
+    L.order = 2;
+  }
+  if (L.order == 2 && !A->rnz) {
+    if (tile && tile->order == 2) return ROSKO_ERR_UNSUPPORTED;
+    L.order = 1;
+    L.V = sparse_default_V(p, A->m_r, 1);
+  }
+  if (L.order == 3) {
+    if (tile && tile->m_c > 0 && tile->m_c != 128) return ROSKO_ERR_INVALID_ARG;
+    L.W = 8;
+  }
   if (L.W < 1 || L.W > 8 || L.KC < 8 || L.KC > 256 || L.KC % 8 != 0 || L.split < 1 ||
       L.split > 65535)
     return ROSKO_ERR_INVALID_ARG;
-  if (!sparse_config_supported(p, b_dtype, c_dtype, L.R, L.V)) return ROSKO_ERR_UNSUPPORTED;
+  if (L.order == 2 && !sparse_config_supported(p, b_dtype, c_dtype, L.R, L.V, 2) &&
+      !(tile && tile->order == 2)) {
+    // no row-slot variant for this panel height: Alg. 2's column order
+    L.order = 1;
+    if (!(tile && tile->n_r > 0)) L.V = sparse_default_V(p, A->m_r, 1);
+  }
+  if (!sparse_config_supported(p, b_dtype, c_dtype, L.R, L.V, L.order))
+    return ROSKO_ERR_UNSUPPORTED;
   // B ring: up to 4 slabs, at least 2, within ~200 KB of shared memory
   const size_t stage_bytes = (size_t)L.KC * 32 * L.V * bsz;
   L.stages = (int)std::min<size_t>(4, (200 * 1024) / stage_bytes);
   if (L.stages < 2) return ROSKO_ERR_INVALID_ARG;
+
+  // one zero fill of C serves every kernel that adds partial sums atomically
+  const bool zero_c =
+      !accumulate && ((n_sparse > 0 && L.split > 1) ||
+                      (n_dense > 0 && dense_needs_zero(n_dense, N, A->K, t.dense_n_r,
+                                                       t.dense_split_k)));
+  if (zero_c && cudaMemset2DAsync(C_dev, (size_t)ldc * csz, 0, (size_t)N * csz, (size_t)A->M,
+                                  st) != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  if (n_dense > 0) {
+    rosko_status s = dense_spmm_launch(A->dense_A, A->n_copy * 128, A->Kpad, A->tile_order_dev,
+                                       n_dense, A->K, B_dev, N, ldb, static_cast<float*>(C_dev),
+                                       ldc, A->M, accumulate, t.dense_n_r, t.dense_split_k,
+                                       zero_c, st);
+    if (s != ROSKO_OK) return s;
+  }
+  if (L.order == 3) {
+    // work list of 128-row tiles: those not taken by the dense path (the
+    // density-sorted tile order's tail), or every tile
+    const int64_t T = (A->M + 127) / 128;
+    const int32_t* list = A->tile_order_dev ? A->tile_order_dev + n_dense : nullptr;
+    return sparse_spmm_launch(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc,
+                              accumulate, L, list, T - n_dense, zero_c, st);
+  }
   return sparse_spmm_launch(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc,
-                            accumulate, L, st);
+                            accumulate, L, A->panel_order_dev, n_sparse, zero_c, st);
+}
+
+
+rosko_status spmm_forced(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N, int64_t ldb,
+                         const float* col_scale, void* C, rosko_dtype c_dt, int64_t ldc,
+                         const rosko_tile* t, cudaStream_t st) {
+  return spmm_run(h, B, b_dt, N, ldb, col_scale, C, c_dt, ldc, 0, t, st);
+}
+}  // namespace rosko
+
+extern "C" {
+
+rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                        int64_t ldb, const float* col_scale_dev, void* C_dev,
+                        rosko_dtype c_dtype, int64_t ldc, int accumulate,
+                        const rosko_tile* tile, rosko_stream_t stream) {
+  bool done = false;
+  rosko_status v = spmm_validate(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc,
+                                 accumulate, static_cast<cudaStream_t>(stream), &done);
+  if (v != ROSKO_OK || done) return v;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int mode = tile ? tile->mode : ROSKO_SCHED_ANALYTIC;
+  if (mode == ROSKO_SCHED_AUTOTUNE || mode == ROSKO_SCHED_LEARNED) {
+    rosko_tile chosen{};
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lk(A->mu);
+      auto it = A->sched_cache.find(N * 4 + mode);
+      if (it != A->sched_cache.end()) {
+        chosen = it->second;
+        have = true;
+      }
+    }
+    if (!have && mode == ROSKO_SCHED_AUTOTUNE && !accumulate) {
+      // the search writes C, which this call overwrites anyway
+      rosko_status s = autotune_impl(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype,
+                                     ldc, 3, &chosen, nullptr, nullptr, st);
+      if (s != ROSKO_OK) return s;
+      have = true;
+    }
+    if (!have && mode == ROSKO_SCHED_LEARNED) {
+      rosko_status s = select_learned(A, N, &chosen, st);
+      if (s == ROSKO_OK) have = true;
+      else if (s != ROSKO_ERR_UNSUPPORTED) return s;
+    }
+    if (have) {
+      {
+        std::lock_guard<std::mutex> lk(A->mu);
+        A->sched_cache[N * 4 + mode] = chosen;
+      }
+      return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,
+                      &chosen, st);
+    }
+    // no cached choice and none can be made here: the analytic rule
+    return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,
+                    nullptr, st);
+  }
+  return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate, tile,
+                  st);
 }
 
 rosko_status rosko_unpack(rosko_packed_t A, void* A_dev_out, int64_t lda, rosko_stream_t stream) {
@@ -286,8 +499,10 @@ rosko_status rosko_packed_info(rosko_packed_t A, int64_t* nnz, int64_t* bytes, i
   if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
   if (nnz) *nnz = A->nnz;
   // values + 1-byte rows + per column (col_ind, start) + panel offsets
+  // device-format bytes the SpMM reads: nonzero records, column records and
+  // panel offsets
   if (bytes)
-    *bytes = A->nnz * (int64_t)(dtype_size(A->dt) + 1) + A->n_cols * 8 + (A->P + 1) * 4 + 4;
+    *bytes = A->nnz * (int64_t)rec_size(A->dt) + (A->n_cols + 1) * 8 + (A->P + 1) * 4;
   if (touched_k) *touched_k = A->touched_k;
   if (n_panels) *n_panels = A->P;
   if (m_r) *m_r = A->m_r;
@@ -301,22 +516,44 @@ rosko_status rosko_packed_export(rosko_packed_t A, void* A_p_host, uint8_t* loc_
                                  int64_t* panel_cols_host) {
   if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
   const size_t esz = dtype_size(A->dt);
+  const size_t rsz = rec_size(A->dt);
   if (cudaDeviceSynchronize() != cudaSuccess) return ROSKO_ERR_CUDA;
-  if (A_p_host && A->nnz &&
-      cudaMemcpy(A_p_host, A->vals, (size_t)A->nnz * esz, cudaMemcpyDeviceToHost) != cudaSuccess)
+  std::vector<unsigned char> recs((size_t)A->nnz * rsz);
+  std::vector<int2> cr((size_t)A->n_cols + 1);
+  if (A->nnz && cudaMemcpy(recs.data(), A->nz, recs.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
     return ROSKO_ERR_CUDA;
-  if (loc_m_host && A->nnz &&
-      cudaMemcpy(loc_m_host, A->rows, (size_t)A->nnz, cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpy(cr.data(), A->colrec, cr.size() * sizeof(int2), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
     return ROSKO_ERR_CUDA;
-  if (col_ind_host && A->n_cols &&
-      cudaMemcpy(col_ind_host, A->col_ind, (size_t)A->n_cols * 4, cudaMemcpyDeviceToHost) !=
-          cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  if (nnz_host && A->n_cols) {
-    std::vector<int32_t> cs((size_t)A->n_cols + 1);
-    if (cudaMemcpy(cs.data(), A->col_start, cs.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-      return ROSKO_ERR_CUDA;
-    for (int64_t c = 0; c < A->n_cols; ++c) nnz_host[c] = cs[c + 1] - cs[c];
+  // decode the interleaved records into the canonical Alg. 1 arrays
+  for (int64_t e = 0; e < A->nnz; ++e) {
+    const unsigned char* w = recs.data() + (size_t)e * rsz;
+    uint32_t row = 0;
+    if (A->dt == ROSKO_F32) {
+      std::memcpy(&row, w, 4);
+      if (A_p_host) std::memcpy(static_cast<char*>(A_p_host) + e * esz, w + 4, 4);
+    } else if (A->dt == ROSKO_F64) {
+      std::memcpy(&row, w + 8, 4);
+      if (A_p_host) std::memcpy(static_cast<char*>(A_p_host) + e * esz, w, 8);
+    } else {
+      uint32_t v;
+      std::memcpy(&v, w, 4);
+      row = v & 0xFFFFu;
+      if (A_p_host) {
+        if (A->dt == ROSKO_BF16) {
+          const uint16_t b = (uint16_t)(v >> 16);
+          std::memcpy(static_cast<char*>(A_p_host) + e * 2, &b, 2);
+        } else {
+          const int8_t q = (int8_t)(uint8_t)(v >> 16);
+          static_cast<int8_t*>(A_p_host)[e] = q;
+        }
+      }
+    }
+    if (loc_m_host) loc_m_host[e] = (uint8_t)row;
+  }
+  for (int64_t c = 0; c < A->n_cols; ++c) {
+    if (col_ind_host) col_ind_host[c] = cr[(size_t)c].x;
+    if (nnz_host) nnz_host[c] = cr[(size_t)c + 1].y - cr[(size_t)c].y;
   }
   if (panel_cols_host) {
     std::vector<int32_t> pc((size_t)A->P + 1);
@@ -324,6 +561,36 @@ rosko_status rosko_packed_export(rosko_packed_t A, void* A_p_host, uint8_t* loc_
       return ROSKO_ERR_CUDA;
     for (int64_t i = 0; i <= A->P; ++i) panel_cols_host[i] = pc[i];
   }
+  return ROSKO_OK;
+}
+
+int32_t rosko_num_candidates(void) { return (int32_t)num_candidates(); }
+
+rosko_status rosko_candidate(rosko_packed_t A, int64_t N, int32_t index, rosko_tile* out) {
+  if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
+  if (!out || N < 0 || index < 0 || index >= num_candidates()) return ROSKO_ERR_INVALID_ARG;
+  return candidate_tile(A, N, index, out) ? ROSKO_OK : ROSKO_ERR_UNSUPPORTED;
+}
+
+rosko_status rosko_autotune(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                            int64_t ldb, const float* col_scale_dev, void* C_dev,
+                            rosko_dtype c_dtype, int64_t ldc, int32_t reps, rosko_tile* best,
+                            float* times_ms, rosko_stream_t stream) {
+  if (!best) return ROSKO_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool done = false;
+  rosko_status v = spmm_validate(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, 0,
+                                 st, &done);
+  if (v != ROSKO_OK) return v;
+  if (done) {
+    schedule_analytic(A->M, A->K, N, A->nnz, A->m_r, A->dt, num_sms(), best);
+    return ROSKO_OK;
+  }
+  rosko_status s = autotune_impl(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc,
+                                 reps, best, times_ms, nullptr, st);
+  if (s != ROSKO_OK) return s;
+  std::lock_guard<std::mutex> lk(A->mu);
+  A->sched_cache[N * 4 + ROSKO_SCHED_AUTOTUNE] = *best;
   return ROSKO_OK;
 }
 

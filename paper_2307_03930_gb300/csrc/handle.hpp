@@ -5,6 +5,7 @@
 
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -14,13 +15,24 @@ constexpr int kNumFeatures = 16;
 }  // namespace rosko
 
 // Device layout of a packed A (Alg. 1 per row panel, panels in order):
-//   panel_col[P+1]  first packed column of each panel (int32)
-//   col_ind[n_cols] column index k of each packed column          (Alg. 1 col_ind)
-//   col_start[n_cols+1] first nonzero of each packed column; the column's
-//                   count is col_start[c+1] - col_start[c]         (Alg. 1 nnz)
-//   vals[nnz]       nonzero values in column order, rows ascending (Alg. 1 A_p)
-//   rows[nnz]       panel-relative row of each value (uint8)       (Alg. 1 loc_m)
-//   row_scale[M]    INT8 only: per-row symmetric scale
+//   panel_col[P+1]   first packed column of each panel (int32)
+//   colrec[n_cols+1] int2 {k, start}: the column index of each packed column
+//                    (Alg. 1 col_ind) and the index of its first nonzero; the
+//                    column's count (Alg. 1 nnz) is colrec[c+1].start -
+//                    colrec[c].start; colrec[n_cols] = {INT32_MAX, nnz}
+//   nz[nnz]          one record per nonzero, in column order with rows
+//                    ascending: the value (Alg. 1 A_p) and its panel-relative
+//                    row (Alg. 1 loc_m) interleaved, so one load serves both:
+//                      BF16, INT8: uint32 = value bits << 16 | row
+//                      FP32: uint2 {row, value bits}; FP64: {double, row, pad}
+//   row_scale[M]     INT8 only: per-row symmetric scale
+// Row-slot execution stream (a second order of the same nonzeros, for the
+// row-slot SpMM traversal; built when K < 65280):
+//   rowptr[M+1]      first record of each row (rows in panel order)
+//   rnz[...]         per row, its nonzeros with k ascending, then one sentinel
+//                    record whose k (0xFFFF / INT32_MAX) ends the row:
+//                      BF16, INT8: uint32 = value bits << 16 | k
+//                      FP32: uint2 {k, value bits}; FP64: {double, k, pad}
 struct rosko_packed_s {
   uint64_t magic = 0;
   int device = 0;
@@ -29,36 +41,117 @@ struct rosko_packed_s {
   rosko_dtype dt = ROSKO_F32;
   int64_t nnz = 0, n_cols = 0, touched_k = 0;
   void* meta_base = nullptr;  // panel_col, row_scale, features
-  void* data_base = nullptr;  // col_ind, col_start, vals, rows
+  void* data_base = nullptr;  // colrec, nz
   int32_t* panel_col = nullptr;
-  int32_t* col_ind = nullptr;
-  int32_t* col_start = nullptr;
-  void* vals = nullptr;
-  uint8_t* rows = nullptr;
+  int2* colrec = nullptr;
+  void* nz = nullptr;
   float* row_scale = nullptr;
+  void* row_base = nullptr;     // rowptr, rnz
+  int32_t* rowptr = nullptr;
+  void* rnz = nullptr;
+  // Touched-row gather stream (m_r = 16): per 128-row tile t the distinct
+  // columns its rows touch (the tile's Alg. 1 col_ind), gu_k[gu_start[t] ..
+  // gu_start[t+1]), and per row the records (value, slot) where slot is the
+  // position of k in the tile's list (same rowptr as rnz).
+  void* gather_base = nullptr;
+  int32_t* gu_start = nullptr;
+  int32_t* gu_k = nullptr;
+  void* gnz = nullptr;
+  int64_t gu_total = 0;
   float* feat_dev = nullptr;   // kNumFeatures floats (N-independent part)
   int64_t* panel_nnz_dev = nullptr;  // P+1 nonzero offsets of panels
+  // Dense-panel split (BF16 only).  128-row tiles sorted by density,
+  // descending; the first n_copy of them have a dense BF16 copy in dense_A
+  // (row block c holds tile tile_order[c]).  panel_order lists the panels of
+  // the tiles in the reverse order (ascending density), so for any threshold
+  // the sparse panels are a prefix of it.
+  int64_t n_tiles = 0, n_copy = 0, Kpad = 0;
+  void* dense_base = nullptr;
+  void* dense_A = nullptr;
+  int32_t* tile_order_dev = nullptr;
+  int32_t* panel_order_dev = nullptr;
+  std::vector<int32_t> tile_order;        // host copy
+  std::vector<double> tile_density;       // sorted, descending
+  std::vector<int32_t> tile_panels;       // panels per tile (indexed by tile id)
+  std::vector<int64_t> panel_nnz;         // host copy, P+1 offsets
   std::mutex mu;               // guards the schedule cache
   std::map<int64_t, rosko_tile> sched_cache;  // per N (and mode) chosen tiles
 };
 
 namespace rosko {
+struct RecF64 {
+  double a;
+  int32_t r;
+  int32_t pad;
+};
+// bytes of one nonzero record for a packed dtype
+inline size_t rec_size(rosko_dtype d) {
+  switch (d) {
+    case ROSKO_F32: return 8;
+    case ROSKO_BF16: return 4;
+    case ROSKO_I8: return 4;
+    case ROSKO_F64: return 16;
+    default: return 0;
+  }
+}
 inline bool handle_ok(const rosko_packed_s* h) { return h && h->magic == kHandleMagic; }
 
 // pack.cu
+constexpr int kDenseTileRows = 128;
 rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
                        rosko_dtype p_dt, const float* row_scale_in, int32_t m_r,
-                       cudaStream_t stream, rosko_packed_s** out);
+                       int32_t dense_min_pct, cudaStream_t stream, rosko_packed_s** out);
 rosko_status unpack_impl(rosko_packed_s* h, void* A_out, int64_t lda, cudaStream_t stream);
+rosko_status count_nonzeros(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
+                            cudaStream_t st, int64_t* out);
+constexpr int64_t kRowSlotMaxK = 65280;  // sentinel k = 0xFFFF stays past every slab end
 
 // spmm_sparse.cu
 struct SparseLaunch {
   int R, V, W, KC, stages, split;
+  int order;  // 1 = column order (Alg. 2), 2 = row-slot, 3 = row-slot + gather
 };
 rosko_status sparse_spmm_launch(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N,
                                 int64_t ldb, const float* col_scale, void* C, rosko_dtype c_dt,
                                 int64_t ldc, int accumulate, const SparseLaunch& L,
+                                const int32_t* panel_list, int64_t n_panels, bool c_zeroed,
                                 cudaStream_t stream);
-bool sparse_config_supported(rosko_dtype p_dt, rosko_dtype b_dt, rosko_dtype c_dt, int R, int V);
-int sparse_default_V(rosko_dtype p_dt, int R);
+bool sparse_config_supported(rosko_dtype p_dt, rosko_dtype b_dt, rosko_dtype c_dt, int R, int V,
+                             int order);
+int sparse_default_V(rosko_dtype p_dt, int R, int order);
+
+// spmm_dense_tc.cu
+rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t Kpad,
+                               const int32_t* tile_order_dev, int64_t n_tiles, int64_t K,
+                               const void* B, int64_t N, int64_t ldb, float* C, int64_t ldc,
+                               int64_t M, int accumulate, int TN, int ctas, bool c_zeroed,
+                               cudaStream_t st);
+// stream-K grid size and whether some dense tile is split between CTAs
+int64_t dense_grid(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas);
+bool dense_needs_zero(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas);
+
+// api.cu
+rosko_status spmm_validate(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                           int64_t ldb, const float* col_scale_dev, void* C_dev,
+                           rosko_dtype c_dtype, int64_t ldc, int accumulate, cudaStream_t st,
+                           bool* done);
+rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                      int64_t ldb, const float* col_scale_dev, void* C_dev, rosko_dtype c_dtype,
+                      int64_t ldc, int accumulate, const rosko_tile* tile, cudaStream_t st);
+rosko_status spmm_forced(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N, int64_t ldb,
+                         const float* col_scale, void* C, rosko_dtype c_dt, int64_t ldc,
+                         const rosko_tile* t, cudaStream_t st);
+rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int32_t m_r,
+                               rosko_dtype dt, int sms, rosko_tile* t);
+
+// autotune.cu
+int num_candidates();
+bool candidate_tile(const rosko_packed_s* h, int64_t N, int idx, rosko_tile* t);
+rosko_status autotune_impl(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N,
+                           int64_t ldb, const float* col_scale, void* C, rosko_dtype c_dt,
+                           int64_t ldc, int reps, rosko_tile* best, float* times,
+                           int32_t* n_out, cudaStream_t st);
+
+// selector.cu
+rosko_status select_learned(rosko_packed_s* h, int64_t N, rosko_tile* out, cudaStream_t st);
 }  // namespace rosko

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "handle.hpp"
 
@@ -59,6 +60,61 @@ template <> struct Conv<__nv_bfloat16, __nv_bfloat16> {
 template <> struct Conv<int8_t, int8_t> {
   __device__ static bool get(int8_t a, float, int8_t& out) { out = a; return a != 0; }
 };
+
+// One nonzero record (value + panel-relative row), see handle.hpp.
+__device__ __forceinline__ void put_rec(void* nz, int64_t e, float v, int r) {
+  reinterpret_cast<uint2*>(nz)[e] = make_uint2((uint32_t)r, __float_as_uint(v));
+}
+__device__ __forceinline__ void put_rec(void* nz, int64_t e, __nv_bfloat16 v, int r) {
+  reinterpret_cast<uint32_t*>(nz)[e] = ((uint32_t)__bfloat16_as_ushort(v) << 16) | (uint32_t)r;
+}
+__device__ __forceinline__ void put_rec(void* nz, int64_t e, int8_t v, int r) {
+  reinterpret_cast<uint32_t*>(nz)[e] = ((uint32_t)(uint8_t)v << 16) | (uint32_t)r;
+}
+__device__ __forceinline__ void put_rec(void* nz, int64_t e, double v, int r) {
+  RecF64 w;
+  w.a = v;
+  w.r = r;
+  w.pad = 0;
+  reinterpret_cast<RecF64*>(nz)[e] = w;
+}
+__device__ __forceinline__ float get_val(const void* nz, int64_t e, float) {
+  return __uint_as_float(reinterpret_cast<const uint2*>(nz)[e].y);
+}
+__device__ __forceinline__ __nv_bfloat16 get_val(const void* nz, int64_t e, __nv_bfloat16) {
+  return __ushort_as_bfloat16((unsigned short)(reinterpret_cast<const uint32_t*>(nz)[e] >> 16));
+}
+__device__ __forceinline__ int8_t get_val(const void* nz, int64_t e, int8_t) {
+  return (int8_t)(uint8_t)(reinterpret_cast<const uint32_t*>(nz)[e] >> 16);
+}
+__device__ __forceinline__ double get_val(const void* nz, int64_t e, double) {
+  return reinterpret_cast<const RecF64*>(nz)[e].a;
+}
+__device__ __forceinline__ int get_row(const void* nz, int64_t e, float) {
+  return (int)reinterpret_cast<const uint2*>(nz)[e].x;
+}
+template <class D>
+__device__ __forceinline__ int get_row(const void* nz, int64_t e, D) {
+  return (int)(reinterpret_cast<const uint32_t*>(nz)[e] & 0xFFFFu);
+}
+__device__ __forceinline__ int get_row(const void* nz, int64_t e, double) {
+  return reinterpret_cast<const RecF64*>(nz)[e].r;
+}
+
+// Nonzero count of A (before packing, to choose the default panel height).
+template <class S>
+__global__ void nnz_count_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
+                                 unsigned long long* __restrict__ out) {
+  unsigned long long c = 0;
+  const int64_t total = M * K;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = i / K, k = i - m * K;
+    c += (to_f32(A[m * lda + k]) != 0.0f) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
+}
 
 // Per-row symmetric INT8 scale s_i = max_k |a_ik| / 127 (1 for an all-zero row).
 __global__ void rowscale_kernel(const float* __restrict__ A, int64_t M, int64_t K, int64_t lda,
@@ -188,8 +244,7 @@ __global__ void sum_flags_kernel(const int* __restrict__ f, int64_t n, int* __re
 template <class S, class D>
 __global__ void scatter_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda, int m_r,
                                const float* __restrict__ scale, const int2* __restrict__ off,
-                               int32_t* __restrict__ col_ind, int32_t* __restrict__ col_start,
-                               D* __restrict__ vals, uint8_t* __restrict__ rows,
+                               int2* __restrict__ colrec, void* __restrict__ nz,
                                int32_t* __restrict__ panel_col, int64_t* __restrict__ panel_nnz) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t p = blockIdx.y;
@@ -202,32 +257,182 @@ __global__ void scatter_kernel(const S* __restrict__ A, int64_t M, int64_t K, in
   }
   const int cnt = off[pk + 1].x - o.x;
   if (cnt == 0) return;
-  col_ind[o.y] = (int32_t)k;
-  col_start[o.y] = o.x;
+  colrec[o.y] = make_int2((int32_t)k, o.x);
   const int64_t m0 = p * m_r;
   const int64_t m1 = min(M, m0 + m_r);
   int64_t e = o.x;
   for (int64_t m = m0; m < m1; ++m) {
     D v;
     if (Conv<S, D>::get(A[m * lda + k], scale ? scale[m] : 1.0f, v)) {
-      vals[e] = v;
-      rows[e] = (uint8_t)(m - m0);
+      put_rec(nz, e, v, (int)(m - m0));
       ++e;
+    }
+  }
+}
+
+// Dense BF16 copies of 128-row tiles for the tensor-core dense-panel path:
+// row block c of `out` holds rows tile_order[c]*128 .. +127 of A (zero past M
+// and past K; row stride Kpad).  Values are converted exactly as the packer
+// converts them.
+__device__ __forceinline__ __nv_bfloat16 to_bf16(float a) { return __float2bfloat16_rn(a); }
+__device__ __forceinline__ __nv_bfloat16 to_bf16(__nv_bfloat16 a) { return a; }
+
+template <class S>
+__global__ void densify_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
+                               const int32_t* __restrict__ tile_order, int64_t n_rows,
+                               int64_t Kpad, __nv_bfloat16* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Kpad) return;
+  for (int64_t rr = blockIdx.y; rr < n_rows; rr += gridDim.y) {
+    const int64_t row = (int64_t)tile_order[rr / kDenseTileRows] * kDenseTileRows +
+                        rr % kDenseTileRows;
+    __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+    if (row < M && k < K) v = to_bf16(A[row * lda + k]);
+    out[rr * Kpad + k] = v;
+  }
+}
+
+// Row-slot stream records (value + column k) and the per-row sentinel.
+__device__ __forceinline__ void put_row_rec(void* rnz, int64_t e, float v, int k) {
+  reinterpret_cast<uint2*>(rnz)[e] = make_uint2((uint32_t)k, __float_as_uint(v));
+}
+__device__ __forceinline__ void put_row_rec(void* rnz, int64_t e, __nv_bfloat16 v, int k) {
+  reinterpret_cast<uint32_t*>(rnz)[e] = ((uint32_t)__bfloat16_as_ushort(v) << 16) | (uint32_t)k;
+}
+__device__ __forceinline__ void put_row_rec(void* rnz, int64_t e, int8_t v, int k) {
+  reinterpret_cast<uint32_t*>(rnz)[e] = ((uint32_t)(uint8_t)v << 16) | (uint32_t)k;
+}
+__device__ __forceinline__ void put_row_rec(void* rnz, int64_t e, double v, int k) {
+  RecF64 w;
+  w.a = v;
+  w.r = k;
+  w.pad = 0;
+  reinterpret_cast<RecF64*>(rnz)[e] = w;
+}
+template <class D>
+__device__ __forceinline__ void put_row_sentinel(void* rnz, int64_t e) {
+  if constexpr (sizeof(D) <= 2) {
+    reinterpret_cast<uint32_t*>(rnz)[e] = 0xFFFFu;
+  } else if constexpr (sizeof(D) == 4) {
+    reinterpret_cast<uint2*>(rnz)[e] = make_uint2(0x7FFFFFFFu, 0u);
+  } else {
+    RecF64 w;
+    w.a = 0.0;
+    w.r = 0x7FFFFFFF;
+    w.pad = 0;
+    reinterpret_cast<RecF64*>(rnz)[e] = w;
+  }
+}
+
+// Row-slot pass 1: cnt[row] = (nonzeros of the row + 1 sentinel, 0); one warp
+// per row, lanes over consecutive columns (coalesced).
+template <class S, class D>
+__global__ void row_count_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
+                                 const float* __restrict__ scale, int2* __restrict__ cnt) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const float sc = scale ? scale[row] : 1.0f;
+  int c = 0;
+  for (int64_t k = lane; k < K; k += 32) {
+    D v;
+    c += Conv<S, D>::get(A[row * lda + k], sc, v) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[row] = make_int2(c + 1, 0);
+}
+
+// Row-slot pass 2: write each row's records (k ascending) at the scanned
+// offset, then its sentinel.
+template <class S, class D>
+__global__ void row_write_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
+                                 const float* __restrict__ scale, const int2* __restrict__ off,
+                                 int32_t* __restrict__ rowptr, void* __restrict__ rnz) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const float sc = scale ? scale[row] : 1.0f;
+  int64_t pos = off[row].x;
+  if (lane == 0) rowptr[row] = (int32_t)pos;
+  for (int64_t k0 = 0; k0 < K; k0 += 32) {
+    const int64_t k = k0 + lane;
+    D v;
+    const bool nzf = (k < K) && Conv<S, D>::get(A[row * lda + k], sc, v);
+    const unsigned mask = __ballot_sync(0xffffffffu, nzf);
+    if (nzf) put_row_rec(rnz, pos + __popc(mask & ((1u << lane) - 1u)), v, (int)k);
+    pos += __popc(mask);
+  }
+  if (lane == 0) put_row_sentinel<D>(rnz, pos);
+}
+
+// Gather stream, pass 1: flag[t*K + k] = (1 if any row of 128-row tile t has a
+// nonzero in column k, 0).
+template <class S, class D>
+__global__ void tile_flag_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
+                                 const float* __restrict__ scale, int2* __restrict__ flag) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = blockIdx.y;
+  if (k >= K) return;
+  const int64_t m0 = t * kDenseTileRows, m1 = min(M, m0 + kDenseTileRows);
+  int any = 0;
+  for (int64_t m = m0; m < m1 && !any; ++m) {
+    D v;
+    any = Conv<S, D>::get(A[m * lda + k], scale ? scale[m] : 1.0f, v) ? 1 : 0;
+  }
+  flag[t * K + k] = make_int2(any, 0);
+}
+
+// Gather stream, pass 2: the union lists gu_k and their per-tile offsets from
+// the scanned flags.
+__global__ void tile_union_kernel(const int2* __restrict__ off, int64_t K, int64_t T,
+                                  int32_t* __restrict__ gu_start, int32_t* __restrict__ gu_k) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = blockIdx.y;
+  if (k >= K) return;
+  const int64_t i = t * K + k;
+  if (k == 0) gu_start[t] = off[i].x;
+  if (off[i + 1].x != off[i].x) gu_k[off[i].x] = (int32_t)k;
+}
+
+// Gather stream, pass 3: each row-slot record re-addressed by its slot in the
+// tile's union list (same positions as the row-slot stream).
+template <class D>
+__global__ void gather_records_kernel(const int32_t* __restrict__ rowptr, const void* __restrict__ rnz,
+                                      const int2* __restrict__ off, int64_t M, int64_t K,
+                                      void* __restrict__ gnz) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const int64_t t = row / kDenseTileRows;
+  const int32_t base = off[t * K].x;
+  const int32_t e0 = rowptr[row], e1 = rowptr[row + 1];   // last entry: sentinel
+  for (int32_t e = e0 + lane; e < e1; e += 32) {
+    if constexpr (sizeof(D) <= 2) {
+      const uint32_t w = reinterpret_cast<const uint32_t*>(rnz)[e];
+      const uint32_t k = w & 0xFFFFu;
+      const uint32_t slot = (e == e1 - 1) ? 0xFFFFu : (uint32_t)(off[t * K + k].x - base);
+      reinterpret_cast<uint32_t*>(gnz)[e] = (w & 0xFFFF0000u) | slot;
+    } else if constexpr (sizeof(D) == 4) {
+      uint2 w = reinterpret_cast<const uint2*>(rnz)[e];
+      if (e != e1 - 1) w.x = (uint32_t)(off[t * K + w.x].x - base);
+      reinterpret_cast<uint2*>(gnz)[e] = w;
+    } else {
+      RecF64 w = reinterpret_cast<const RecF64*>(rnz)[e];
+      if (e != e1 - 1) w.r = off[t * K + w.r].x - base;
+      reinterpret_cast<RecF64*>(gnz)[e] = w;
     }
   }
 }
 
 template <class D>
 __global__ void unpack_kernel(const int32_t* __restrict__ panel_col,
-                              const int32_t* __restrict__ col_ind,
-                              const int32_t* __restrict__ col_start, const D* __restrict__ vals,
-                              const uint8_t* __restrict__ rows, int m_r, int64_t lda,
-                              D* __restrict__ out) {
+                              const int2* __restrict__ colrec, const void* __restrict__ nz,
+                              int m_r, int64_t lda, D* __restrict__ out) {
   const int64_t p = blockIdx.x;
   for (int64_t c = panel_col[p] + threadIdx.x; c < panel_col[p + 1]; c += blockDim.x) {
-    const int64_t k = col_ind[c];
-    for (int32_t e = col_start[c]; e < col_start[c + 1]; ++e)
-      out[(p * m_r + rows[e]) * lda + k] = vals[e];
+    const int64_t k = colrec[c].x;
+    for (int32_t e = colrec[c].y; e < colrec[c + 1].y; ++e)
+      out[(p * m_r + get_row(nz, e, D())) * lda + k] = get_val(nz, e, D());
   }
 }
 
@@ -239,6 +444,10 @@ struct Scratch {
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <class S, class D>
+rosko_status build_row_stream(const S* A, int64_t lda, const float* scale, rosko_packed_s* h,
+                              cudaStream_t st);
 
 template <class S, class D>
 rosko_status pack_typed(const S* A, int64_t M, int64_t K, int64_t lda, const float* scale_in,
@@ -328,30 +537,26 @@ rosko_status pack_typed(const S* A, int64_t M, int64_t K, int64_t lda, const flo
   h->n_cols = host_tot[1];
   h->touched_k = host_tot[2];
 
-  const size_t esz = sizeof(D);
-  const size_t d_ci = 0;
-  const size_t d_cs = align_up(d_ci + (size_t)h->n_cols * 4, 256);
-  const size_t d_v = align_up(d_cs + (size_t)(h->n_cols + 1) * 4, 256);
-  const size_t d_r = align_up(d_v + (size_t)h->nnz * esz, 256);
-  const size_t data_bytes = d_r + align_up((size_t)h->nnz, 16) + 256;
+  const size_t rsz = rec_size(h->dt);
+  const size_t d_cr = 0;
+  const size_t d_nz = align_up(d_cr + (size_t)(h->n_cols + 2) * 8, 256);
+  const size_t data_bytes = d_nz + (size_t)(h->nnz + 1) * rsz + 256;
   if (dev_malloc(&h->data_base, data_bytes) != cudaSuccess) return ROSKO_ERR_OOM;
   char* db = static_cast<char*>(h->data_base);
-  h->col_ind = reinterpret_cast<int32_t*>(db + d_ci);
-  h->col_start = reinterpret_cast<int32_t*>(db + d_cs);
-  h->vals = db + d_v;
-  h->rows = reinterpret_cast<uint8_t*>(db + d_r);
+  h->colrec = reinterpret_cast<int2*>(db + d_cr);
+  h->nz = db + d_nz;
 
   if (n > 0)
-    scatter_kernel<S, D><<<grid, T, 0, st>>>(A, M, K, lda, h->m_r, scale, cnt, h->col_ind,
-                                             h->col_start, reinterpret_cast<D*>(h->vals), h->rows,
+    scatter_kernel<S, D><<<grid, T, 0, st>>>(A, M, K, lda, h->m_r, scale, cnt, h->colrec, h->nz,
                                              h->panel_col, h->panel_nnz_dev);
   if (n > 0) count_launches(1);
-  // tails: panel_col[P] = n_cols, panel_nnz[P] = nnz, col_start[n_cols] = nnz
-  int32_t tail32[2] = {(int32_t)h->n_cols, (int32_t)h->nnz};
+  // tails: panel_col[P] = n_cols, panel_nnz[P] = nnz, colrec[n_cols] = {INT32_MAX, nnz}
+  int32_t tail32[1] = {(int32_t)h->n_cols};
+  int2 tailrec[2] = {make_int2(INT32_MAX, (int32_t)h->nnz), make_int2(INT32_MAX, (int32_t)h->nnz)};
   int64_t tail64 = h->nnz;
   if (cudaMemcpyAsync(h->panel_col + P, &tail32[0], 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(h->col_start + h->n_cols, &tail32[1], 4, cudaMemcpyHostToDevice, st) !=
-          cudaSuccess ||
+      cudaMemcpyAsync(h->colrec + h->n_cols, tailrec, sizeof(tailrec), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess ||
       cudaMemcpyAsync(h->panel_nnz_dev + P, &tail64, 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return ROSKO_ERR_CUDA;
   if (P == 0 || K == 0) {
@@ -363,6 +568,155 @@ rosko_status pack_typed(const S* A, int64_t M, int64_t K, int64_t lda, const flo
   // the scratch and the host tails above must outlive the queued work
   if (cudaStreamSynchronize(st) != cudaSuccess) return ROSKO_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return ROSKO_ERR_CUDA;
+  return build_row_stream<S, D>(A, lda, scale, h, st);
+}
+
+// Exclusive scan of n int2 in place (data[n] receives the total); `sums`
+// holds at least (n + kScanTile - 1) / kScanTile + 1 entries.
+void run_scan(int2* data, int64_t n, int2* sums, cudaStream_t st) {
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, sums);
+  scan_spine_kernel<<<1, kScanThreads, 0, st>>>(sums, nb);
+  scan_down_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, sums, nb);
+  count_launches(3);
+}
+
+// Row-slot execution stream: the same nonzeros ordered by (row, k), one
+// sentinel per row.  Needs K < kRowSlotMaxK (16-bit k in 32-bit records).
+template <class S, class D>
+rosko_status build_row_stream(const S* A, int64_t lda, const float* scale, rosko_packed_s* h,
+                              cudaStream_t st) {
+  const int64_t M = h->M, K = h->K;
+  if (M == 0 || K >= kRowSlotMaxK) return ROSKO_OK;
+  const int64_t nb = (M + kScanTile - 1) / kScanTile;
+  Scratch scr;
+  const size_t o_sum = align_up((size_t)(M + 1) * sizeof(int2), 256);
+  if (dev_malloc(&scr.p, o_sum + (size_t)(nb + 1) * sizeof(int2)) != cudaSuccess)
+    return ROSKO_ERR_OOM;
+  int2* cnt = static_cast<int2*>(scr.p);
+  int2* sums = reinterpret_cast<int2*>(static_cast<char*>(scr.p) + o_sum);
+  const size_t rsz = rec_size(h->dt);
+  const size_t o_rnz = align_up((size_t)(M + 1) * 4, 256);
+  const size_t bytes = o_rnz + (size_t)(h->nnz + M) * rsz + 256;
+  if (dev_malloc(&h->row_base, bytes) != cudaSuccess) return ROSKO_ERR_OOM;
+  h->rowptr = static_cast<int32_t*>(h->row_base);
+  h->rnz = static_cast<char*>(h->row_base) + o_rnz;
+  const int wpb = 8;
+  const unsigned blocks = (unsigned)((M + wpb - 1) / wpb);
+  row_count_kernel<S, D><<<blocks, wpb * 32, 0, st>>>(A, M, K, lda, scale, cnt);
+  count_launches(1);
+  run_scan(cnt, M, sums, st);
+  row_write_kernel<S, D><<<blocks, wpb * 32, 0, st>>>(A, M, K, lda, scale, cnt, h->rowptr,
+                                                      h->rnz);
+  count_launches(1);
+  const int32_t tail = (int32_t)(h->nnz + M);
+  if (cudaMemcpyAsync(h->rowptr + M, &tail, 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  if (h->m_r != 16 || K == 0) return ROSKO_OK;
+
+  // touched-row gather stream: per 128-row tile, the union of its columns
+  const int64_t T = (M + kDenseTileRows - 1) / kDenseTileRows;
+  const int64_t n = T * K;
+  const int64_t nbt = (n + kScanTile - 1) / kScanTile;
+  Scratch fs;
+  const size_t f_sum = align_up((size_t)(n + 1) * sizeof(int2), 256);
+  if (dev_malloc(&fs.p, f_sum + (size_t)(nbt + 1) * sizeof(int2)) != cudaSuccess)
+    return ROSKO_ERR_OOM;
+  int2* flag = static_cast<int2*>(fs.p);
+  int2* fsums = reinterpret_cast<int2*>(static_cast<char*>(fs.p) + f_sum);
+  const dim3 g2((unsigned)((K + 255) / 256), (unsigned)T);
+  tile_flag_kernel<S, D><<<g2, 256, 0, st>>>(A, M, K, lda, scale, flag);
+  count_launches(1);
+  run_scan(flag, n, fsums, st);
+  int2 tot;
+  if (cudaMemcpyAsync(&tot, flag + n, sizeof(int2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  h->gu_total = tot.x;
+  const size_t o_k = align_up((size_t)(T + 1) * 4, 256);
+  const size_t o_g = align_up(o_k + (size_t)std::max<int64_t>(tot.x, 1) * 4, 256);
+  if (dev_malloc(&h->gather_base, o_g + (size_t)(h->nnz + M) * rsz + 256) != cudaSuccess)
+    return ROSKO_ERR_OOM;
+  char* gb = static_cast<char*>(h->gather_base);
+  h->gu_start = reinterpret_cast<int32_t*>(gb);
+  h->gu_k = reinterpret_cast<int32_t*>(gb + o_k);
+  h->gnz = gb + o_g;
+  tile_union_kernel<<<g2, 256, 0, st>>>(flag, K, T, h->gu_start, h->gu_k);
+  gather_records_kernel<D><<<blocks, wpb * 32, 0, st>>>(h->rowptr, h->rnz, flag, M, K, h->gnz);
+  count_launches(2);
+  const int32_t gtail = tot.x;
+  if (cudaMemcpyAsync(h->gu_start + T, &gtail, 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  return ROSKO_OK;
+}
+
+// Dense-panel split bookkeeping and dense copies (BF16 packs only).
+template <class S>
+rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pct, rosko_packed_s* h,
+                               cudaStream_t st) {
+  const int64_t M = h->M, K = h->K, P = h->P;
+  if (M == 0 || K == 0) return ROSKO_OK;
+  h->panel_nnz.assign((size_t)P + 1, 0);
+  if (cudaMemcpy(h->panel_nnz.data(), h->panel_nnz_dev, (size_t)(P + 1) * 8,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  const int64_t T = (M + kDenseTileRows - 1) / kDenseTileRows;
+  const int64_t ppt = kDenseTileRows / h->m_r;
+  std::vector<double> dens((size_t)T);
+  h->tile_panels.assign((size_t)T, 0);
+  for (int64_t t = 0; t < T; ++t) {
+    const int64_t p0 = t * ppt, p1 = std::min<int64_t>(P, p0 + ppt);
+    const int64_t rows = std::min<int64_t>(kDenseTileRows, M - t * kDenseTileRows);
+    dens[(size_t)t] = (double)(h->panel_nnz[(size_t)p1] - h->panel_nnz[(size_t)p0]) /
+                      ((double)rows * (double)K);
+    h->tile_panels[(size_t)t] = (int32_t)(p1 - p0);
+  }
+  h->tile_order.resize((size_t)T);
+  for (int64_t t = 0; t < T; ++t) h->tile_order[(size_t)t] = (int32_t)t;
+  std::stable_sort(h->tile_order.begin(), h->tile_order.end(),
+                   [&](int32_t a, int32_t b) { return dens[(size_t)a] > dens[(size_t)b]; });
+  h->tile_density.resize((size_t)T);
+  int64_t n_copy = 0;
+  for (int64_t c = 0; c < T; ++c) {
+    h->tile_density[(size_t)c] = dens[(size_t)h->tile_order[(size_t)c]];
+    if (h->tile_density[(size_t)c] * 100.0 >= (double)dense_min_pct) n_copy = c + 1;
+  }
+  std::vector<int32_t> panel_order;
+  panel_order.reserve((size_t)P);
+  for (int64_t c = T - 1; c >= 0; --c) {
+    const int64_t t = h->tile_order[(size_t)c];
+    for (int64_t q = 0; q < h->tile_panels[(size_t)t]; ++q)
+      panel_order.push_back((int32_t)(t * ppt + q));
+  }
+  h->n_tiles = T;
+  h->n_copy = n_copy;
+  h->Kpad = (K + 7) / 8 * 8;
+  const size_t o_to = 0;
+  const size_t o_po = align_up(o_to + (size_t)T * 4, 256);
+  const size_t o_da = align_up(o_po + (size_t)P * 4, 1024);
+  const size_t bytes = o_da + (size_t)n_copy * kDenseTileRows * (size_t)h->Kpad * 2 + 256;
+  if (dev_malloc(&h->dense_base, bytes) != cudaSuccess) return ROSKO_ERR_OOM;
+  char* b = static_cast<char*>(h->dense_base);
+  h->tile_order_dev = reinterpret_cast<int32_t*>(b + o_to);
+  h->panel_order_dev = reinterpret_cast<int32_t*>(b + o_po);
+  h->dense_A = b + o_da;
+  if (cudaMemcpyAsync(h->tile_order_dev, h->tile_order.data(), (size_t)T * 4,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(h->panel_order_dev, panel_order.data(), (size_t)P * 4,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  if (n_copy > 0) {
+    const int64_t rows = n_copy * kDenseTileRows;
+    const dim3 grid((unsigned)((h->Kpad + 255) / 256), (unsigned)std::min<int64_t>(rows, 65535));
+    densify_kernel<S><<<grid, 256, 0, st>>>(A, M, K, lda, h->tile_order_dev, rows, h->Kpad,
+                                            reinterpret_cast<__nv_bfloat16*>(h->dense_A));
+    count_launches(1);
+  }
+  // host vectors are staged by the copies above; wait before they go away
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return ROSKO_ERR_CUDA;
   return ROSKO_OK;
 }
 
@@ -370,7 +724,7 @@ rosko_status pack_typed(const S* A, int64_t M, int64_t K, int64_t lda, const flo
 
 rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
                        rosko_dtype p_dt, const float* row_scale_in, int32_t m_r,
-                       cudaStream_t stream, rosko_packed_s** out) {
+                       int32_t dense_min_pct, cudaStream_t stream, rosko_packed_s** out) {
   rosko_packed_s* h = new (std::nothrow) rosko_packed_s();
   if (!h) return ROSKO_ERR_OOM;
   cudaGetDevice(&h->device);
@@ -393,14 +747,49 @@ rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, in
                                                  false, h, stream);
   else if (a_dt == ROSKO_I8 && p_dt == ROSKO_I8)
     s = pack_typed<int8_t, int8_t>((const int8_t*)A, M, K, lda, row_scale_in, false, h, stream);
+  if (s == ROSKO_OK && p_dt == ROSKO_BF16 && dense_min_pct <= 100) {
+    if (a_dt == ROSKO_F32)
+      s = build_dense_tiles<float>((const float*)A, lda, dense_min_pct, h, stream);
+    else
+      s = build_dense_tiles<__nv_bfloat16>((const __nv_bfloat16*)A, lda, dense_min_pct, h,
+                                           stream);
+  }
   if (s != ROSKO_OK) {
     if (h->meta_base) cudaFree(h->meta_base);
     if (h->data_base) cudaFree(h->data_base);
+    if (h->dense_base) cudaFree(h->dense_base);
+    if (h->row_base) cudaFree(h->row_base);
+    if (h->gather_base) cudaFree(h->gather_base);
     delete h;
     return s;
   }
   h->magic = kHandleMagic;
   *out = h;
+  return ROSKO_OK;
+}
+
+rosko_status count_nonzeros(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
+                            cudaStream_t st, int64_t* out) {
+  *out = 0;
+  if (M == 0 || K == 0) return ROSKO_OK;
+  Scratch scr;
+  if (dev_malloc(&scr.p, 256) != cudaSuccess) return ROSKO_ERR_OOM;
+  auto* d = static_cast<unsigned long long*>(scr.p);
+  if (cudaMemsetAsync(d, 0, 8, st) != cudaSuccess) return ROSKO_ERR_CUDA;
+  const int64_t total = M * K;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4 * 1024);
+  if (a_dt == ROSKO_F32)
+    nnz_count_kernel<float><<<blocks, 256, 0, st>>>((const float*)A, M, K, lda, d);
+  else if (a_dt == ROSKO_BF16)
+    nnz_count_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)A, M, K, lda, d);
+  else
+    return ROSKO_ERR_UNSUPPORTED;
+  count_launches(1);
+  unsigned long long v = 0;
+  if (cudaMemcpyAsync(&v, d, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  *out = (int64_t)v;
   return ROSKO_OK;
 }
 
@@ -414,23 +803,19 @@ rosko_status unpack_impl(rosko_packed_s* h, void* A_out, int64_t lda, cudaStream
   const unsigned g = (unsigned)h->P;
   switch (h->dt) {
     case ROSKO_F32:
-      unpack_kernel<float><<<g, 256, 0, st>>>(h->panel_col, h->col_ind, h->col_start,
-                                              (const float*)h->vals, h->rows, h->m_r, lda,
+      unpack_kernel<float><<<g, 256, 0, st>>>(h->panel_col, h->colrec, h->nz, h->m_r, lda,
                                               (float*)A_out);
       break;
     case ROSKO_BF16:
-      unpack_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(h->panel_col, h->col_ind, h->col_start,
-                                                      (const __nv_bfloat16*)h->vals, h->rows,
-                                                      h->m_r, lda, (__nv_bfloat16*)A_out);
+      unpack_kernel<__nv_bfloat16><<<g, 256, 0, st>>>(h->panel_col, h->colrec, h->nz, h->m_r,
+                                                      lda, (__nv_bfloat16*)A_out);
       break;
     case ROSKO_I8:
-      unpack_kernel<int8_t><<<g, 256, 0, st>>>(h->panel_col, h->col_ind, h->col_start,
-                                               (const int8_t*)h->vals, h->rows, h->m_r, lda,
+      unpack_kernel<int8_t><<<g, 256, 0, st>>>(h->panel_col, h->colrec, h->nz, h->m_r, lda,
                                                (int8_t*)A_out);
       break;
     case ROSKO_F64:
-      unpack_kernel<double><<<g, 256, 0, st>>>(h->panel_col, h->col_ind, h->col_start,
-                                               (const double*)h->vals, h->rows, h->m_r, lda,
+      unpack_kernel<double><<<g, 256, 0, st>>>(h->panel_col, h->colrec, h->nz, h->m_r, lda,
                                                (double*)A_out);
       break;
     default:

@@ -1,11 +1,11 @@
 // Sparse SpMM on CUDA cores: Alg. 2 (packed row-skipping outer product).
 //
 // Mapping of Alg. 2 and the tiling of Sec. 4.2 onto one SM:
-//   * one warp owns one packed row panel (m_r = R rows) and keeps the
-//     R x (32 V) C tile in registers (each lane: R rows x V columns) for the
-//     whole K range (K-first schedule, Sec. 2.2 / 4.2);
+//   * one warp owns one packed row panel (m_r = R rows) and keeps an
+//     R x (32 V) tile of C in registers (each lane: R rows x V columns) for
+//     the whole K range of its CTA (K-first schedule, Sec. 2.2 / 4.2);
 //   * a CTA is W such warps (m_c = W R rows of C) plus one producer warp that
-//     streams k_c x n_r slabs of B into shared memory with TMA, through a ring
+//     streams k_c x n_r slabs of B into shared memory with TMA through a ring
 //     of `stages` buffers guarded by full/empty mbarriers (the B block that
 //     Sec. 4.2 broadcasts from L3 to the cores);
 //   * for every packed column k of its panel inside the slab a warp loads the
@@ -13,10 +13,15 @@
 //     each of the column's nonzeros, multiply-accumulates it into the C row
 //     named by loc_m.  Registers cannot be indexed at run time, so the row is
 //     resolved by a warp-uniform switch over the R register rows (all lanes
-//     share the nonzero, so there is no divergence);
+//     share the nonzero, so there is no divergence).  Each dispatch feeds V
+//     FMAs per lane, so wide strips (V = 8..16) amortise it;
+//   * a lane's V columns are V/CE chunks of CE = 16 bytes / sizeof(B) values
+//     spaced 32 CE apart, so every shared-memory load of the warp reads one
+//     contiguous 512-byte run (conflict free);
 //   * C is written once at the end (or added with atomics when K is split
 //     across CTAs).
 #include <algorithm>
+#include <climits>
 
 #include "handle.hpp"
 
@@ -24,16 +29,21 @@ namespace rosko {
 namespace {
 
 struct SparseParams {
+  const int32_t* panel_list;  // panels to process (NULL: 0 .. n_list-1)
+  int64_t n_list;
   const int32_t* panel_col;
-  const int32_t* col_ind;
-  const int32_t* col_start;
-  const void* vals;
-  const uint8_t* rows;
+  const int2* colrec;
+  const void* nz;
+  const int32_t* rowptr;  // row-slot stream
+  const void* rnz;
+  const int32_t* gu_start;  // gather stream (order 3)
+  const int32_t* gu_k;
+  const void* gnz;
   const float* row_scale;
   const float* col_scale;
   void* C;
   int64_t ldc, M, N, P;
-  int W, KC, stages, split, slabs_total;
+  int W, KC, stages, split, slabs_total, boxes;
   int load_c_first, add_c_at_end, atomic_out, vec_ok;
   int* status;
 };
@@ -44,27 +54,68 @@ template <> struct AccOf<__nv_bfloat16> { using type = float; };
 template <> struct AccOf<int8_t> { using type = int32_t; };
 template <> struct AccOf<double> { using type = double; };
 
+// Nonzero records (see handle.hpp) and their decoding.
+template <class TA> struct Rec;
+template <> struct Rec<float> {
+  using T = uint2;
+  __device__ static float a(T w) { return __uint_as_float(w.y); }
+  __device__ static int r(T w) { return (int)w.x; }
+};
+template <> struct Rec<__nv_bfloat16> {
+  using T = uint32_t;
+  __device__ static float a(T w) { return __uint_as_float(w & 0xFFFF0000u); }
+  __device__ static int r(T w) { return (int)(w & 0xFFFFu); }
+};
+template <> struct Rec<int8_t> {
+  using T = uint32_t;
+  __device__ static int32_t a(T w) { return (int32_t)(int8_t)(uint8_t)(w >> 16); }
+  __device__ static int r(T w) { return (int)(w & 0xFFFFu); }
+};
+template <> struct Rec<double> {
+  using T = RecF64;
+  __device__ static double a(const T& w) { return w.a; }
+  __device__ static int r(const T& w) { return w.r; }
+};
+
+// Row-slot records (value + column k, see handle.hpp) and their decoding.
+template <class TA> struct RowRec;
+template <> struct RowRec<float> {
+  using T = uint2;
+  __device__ static float a(T w) { return __uint_as_float(w.y); }
+  __device__ static int k(T w) { return (int)w.x; }
+};
+template <> struct RowRec<__nv_bfloat16> {
+  using T = uint32_t;
+  __device__ static float a(T w) { return __uint_as_float(w & 0xFFFF0000u); }
+  __device__ static int k(T w) { return (int)(w & 0xFFFFu); }
+};
+template <> struct RowRec<int8_t> {
+  using T = uint32_t;
+  __device__ static int32_t a(T w) { return (int32_t)(int8_t)(uint8_t)(w >> 16); }
+  __device__ static int k(T w) { return (int)(w & 0xFFFFu); }
+};
+template <> struct RowRec<double> {
+  using T = RecF64;
+  __device__ static double a(const T& w) { return w.a; }
+  __device__ static int k(const T& w) { return w.r; }
+};
+
 __device__ __forceinline__ float to_acc(float x, float) { return x; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 x, float) { return __bfloat162float(x); }
 __device__ __forceinline__ int32_t to_acc(int8_t x, int32_t) { return (int32_t)x; }
-__device__ __forceinline__ double to_acc(double x, double) { return x; }
 __device__ __forceinline__ double to_acc(float x, double) { return (double)x; }
 
 __device__ __forceinline__ float mac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double mac(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ int32_t mac(int32_t a, int32_t b, int32_t c) { return a * b + c; }
 
-// V consecutive elements of a staged B row into accumulator-typed registers.
-template <class TB, class TACC, int V>
-__device__ __forceinline__ void load_b(const TB* __restrict__ src, TACC (&b)[V]) {
-  constexpr int BYTES = V * (int)sizeof(TB);
-  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16 || BYTES == 32,
-                "B segment must be 4, 8, 16 or 32 bytes");
-  TB tmp[V];
-  if constexpr (BYTES == 32) {
-    reinterpret_cast<uint4*>(tmp)[0] = reinterpret_cast<const uint4*>(src)[0];
-    reinterpret_cast<uint4*>(tmp)[1] = reinterpret_cast<const uint4*>(src)[1];
-  } else if constexpr (BYTES == 16) {
+// CE consecutive B elements (CE * sizeof(TB) = 4, 8 or 16 bytes) into registers.
+template <class TB, class TACC, int CE>
+__device__ __forceinline__ void load_chunk(const TB* __restrict__ src, TACC* b) {
+  constexpr int BYTES = CE * (int)sizeof(TB);
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "chunk must be 4, 8 or 16 bytes");
+  TB tmp[CE];
+  if constexpr (BYTES == 16) {
     *reinterpret_cast<uint4*>(tmp) = *reinterpret_cast<const uint4*>(src);
   } else if constexpr (BYTES == 8) {
     *reinterpret_cast<uint2*>(tmp) = *reinterpret_cast<const uint2*>(src);
@@ -72,7 +123,7 @@ __device__ __forceinline__ void load_b(const TB* __restrict__ src, TACC (&b)[V])
     *reinterpret_cast<uint32_t*>(tmp) = *reinterpret_cast<const uint32_t*>(src);
   }
 #pragma unroll
-  for (int v = 0; v < V; ++v) b[v] = to_acc(tmp[v], TACC(0));
+  for (int v = 0; v < CE; ++v) b[v] = to_acc(tmp[v], TACC(0));
 }
 
 // acc[r][:] += a * b[:] for a run-time, warp-uniform row r < R.
@@ -109,16 +160,36 @@ __device__ __forceinline__ float out_value<float, int32_t>(int32_t acc, const Sp
   return ((float)acc * p.row_scale[row]) * p.col_scale[col];
 }
 
-template <class TC>
-__device__ __forceinline__ void atomic_add_out(TC* dst, TC v) {
-  atomicAdd(dst, v);
+template <class TC, int CE>
+__device__ __forceinline__ void store_chunk(TC* dst, const TC* o) {
+  constexpr int OB = CE * (int)sizeof(TC);
+  if constexpr (OB % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < OB / 16; ++i)
+      reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(o)[i];
+  } else if constexpr (OB == 8) {
+    *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(o);
+  } else {
+#pragma unroll
+    for (int i = 0; i < CE; ++i) dst[i] = o[i];
+  }
 }
 
-template <class TA, class TB, class TC, int R, int V>
+template <class TA, class TB, class TC, int R, int V, int ORDER>
 __global__ void __launch_bounds__(288, 1)
-    sparse_spmm_kernel(const SparseParams p, const __grid_constant__ CUtensorMap tmB) {
+    sparse_spmm_kernel(const SparseParams p, const __grid_constant__ CUtensorMap tmB,
+                       const __grid_constant__ CUtensorMap tmB1) {
   using TACC = typename AccOf<TA>::type;
+  using RT = typename Rec<TA>::T;
   constexpr int NR = 32 * V;
+  // a lane chunk is at most 16 bytes and at most 8 elements, so that the
+  // warp's 32 chunks (<= 256 elements) never straddle a TMA box
+  constexpr int G = (16 / (int)sizeof(TB)) < 8 ? (16 / (int)sizeof(TB)) : 8;
+  constexpr int CE = V < G ? V : G;                // elements per lane chunk
+  constexpr int J = V / CE;                        // chunks per lane
+  constexpr int BOXW = NR > 256 ? 256 : NR;        // width of one TMA box
+  static_assert(J * CE == V, "V must be a multiple of the chunk width");
+  static_assert(BOXW % (32 * CE) == 0, "warp chunks must tile a box");
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + p.stages;
@@ -128,9 +199,20 @@ __global__ void __launch_bounds__(288, 1)
   const int W = p.W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n0 = (int64_t)blockIdx.y * NR;
-  const int s_per = (p.slabs_total + p.split - 1) / p.split;
+  // order 3: this CTA is one 128-row tile and its slabs are slots of the
+  // tile's touched-column list
+  int64_t tile = 0;
+  int ustart = 0, ulen = 0;
+  int slabs_total = p.slabs_total;
+  if constexpr (ORDER == 3) {
+    tile = p.panel_list ? (int64_t)__ldg(&p.panel_list[blockIdx.x]) : (int64_t)blockIdx.x;
+    ustart = __ldg(&p.gu_start[tile]);
+    ulen = __ldg(&p.gu_start[tile + 1]) - ustart;
+    slabs_total = (ulen + p.KC - 1) / p.KC;
+  }
+  const int s_per = (slabs_total + p.split - 1) / p.split;
   const int s_begin = (int)blockIdx.z * s_per;
-  const int nslabs = max(0, min(p.slabs_total, s_begin + s_per) - s_begin);
+  const int nslabs = max(0, min(slabs_total, s_begin + s_per) - s_begin);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -141,11 +223,47 @@ __global__ void __launch_bounds__(288, 1)
   }
   __syncthreads();
 
+  if (ORDER == 3 && warp == W) {
+    // ---------------- producer (order 3): gather the tile's touched B rows ---
+    // slab i holds slots [(s_begin+i) k_c, +k_c) of the tile's column list;
+    // the 32 lanes fetch their column indices and issue one row copy each
+    if (nslabs > 0) {
+      if (lane == 0) prefetch_tensormap(&tmB1);
+      const int box_w = BOXW;
+      int i = 0;
+      bool ok = true;
+      for (; i < nslabs; ++i) {
+        const int st = i % p.stages;
+        const uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+        if (i >= p.stages && !mbar_wait_bounded(&empty[st], ph ^ 1u, p.status)) {
+          ok = false;
+          break;
+        }
+        const int slot0 = (s_begin + i) * p.KC;
+        const int rows = min(p.KC, ulen - slot0);
+        if (lane == 0)
+          mbar_arrive_expect_tx(&full[st], (uint32_t)(rows * NR * (int)sizeof(TB)));
+        __syncwarp();
+        for (int j = lane; j < rows; j += 32) {
+          const int k = __ldg(&p.gu_k[ustart + slot0 + j]);
+          for (int bx = 0; bx < p.boxes; ++bx)
+            tma_load_2d(Bs + st * stage_elems + (size_t)bx * box_w * p.KC + (size_t)j * box_w,
+                        &tmB1, (int32_t)(n0 + bx * box_w), k, &full[st]);
+        }
+      }
+      if (!ok && lane == 0) {
+        for (int j = max(0, i - p.stages); j < i; ++j)
+          mbar_wait_bounded(&full[j % p.stages], (uint32_t)(j / p.stages) & 1u, p.status);
+      }
+    }
+    return;
+  }
   if (warp == W) {
     // ---------------- producer: TMA ring over the K slabs of this split -----
     if (lane == 0 && nslabs > 0) {
       prefetch_tensormap(&tmB);
       const uint32_t bytes = (uint32_t)(stage_elems * sizeof(TB));
+      const int box_w = BOXW;
       int i = 0;
       bool ok = true;
       for (; i < nslabs; ++i) {
@@ -156,7 +274,9 @@ __global__ void __launch_bounds__(288, 1)
           break;
         }
         mbar_arrive_expect_tx(&full[st], bytes);
-        tma_load_2d(Bs + st * stage_elems, &tmB, (int32_t)n0, (s_begin + i) * p.KC, &full[st]);
+        for (int bx = 0; bx < p.boxes; ++bx)
+          tma_load_2d(Bs + st * stage_elems + (size_t)bx * box_w * p.KC, &tmB,
+                      (int32_t)(n0 + bx * box_w), (s_begin + i) * p.KC, &full[st]);
       }
       if (!ok) {
         // consumers gave up: wait (bounded) for our copies in flight to land
@@ -168,8 +288,16 @@ __global__ void __launch_bounds__(288, 1)
   }
 
   // ---------------- consumers: one packed row panel per warp -----------------
-  const int64_t panel = (int64_t)blockIdx.x * W + warp;
-  const bool has_panel = panel < p.P;
+  int64_t panel = 0;
+  bool has_panel = false;
+  if constexpr (ORDER == 3) {
+    panel = tile * W + warp;
+    has_panel = panel < p.P;
+  } else {
+    const int64_t slot = (int64_t)blockIdx.x * W + warp;
+    has_panel = slot < p.n_list;
+    panel = !has_panel ? 0 : (p.panel_list ? (int64_t)__ldg(&p.panel_list[slot]) : slot);
+  }
   const int64_t row0 = panel * R;
   TACC acc[R][V];
 #pragma unroll
@@ -178,7 +306,6 @@ __global__ void __launch_bounds__(288, 1)
     for (int v = 0; v < V; ++v) acc[r][v] = TACC(0);
 
   TC* C = reinterpret_cast<TC*>(p.C);
-  const int64_t col0 = n0 + lane * V;
   if (has_panel && p.load_c_first) {
     // Alg. 2 loads the C rows into registers before the outer products
 #pragma unroll
@@ -186,58 +313,127 @@ __global__ void __launch_bounds__(288, 1)
       const int64_t row = row0 + r;
       if (row < p.M)
 #pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (col0 + v < p.N) acc[r][v] = (TACC)C[row * p.ldc + col0 + v];
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+          for (int v = 0; v < CE; ++v) {
+            const int64_t col = n0 + j * 32 * CE + lane * CE + v;
+            if (col < p.N) acc[r][j * CE + v] = (TACC)C[row * p.ldc + col];
+          }
     }
   }
 
-  int c = 0, c_end = 0;
-  if (has_panel) {
-    c = __ldg(&p.panel_col[panel]);
-    c_end = __ldg(&p.panel_col[panel + 1]);
-    if (s_begin > 0) {  // first packed column of this split's K range
-      const int kb = s_begin * p.KC;
-      int lo = c, hi = c_end;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(&p.col_ind[mid]) < kb) lo = mid + 1; else hi = mid;
-      }
-      c = lo;
-    }
-  }
-  const TA* __restrict__ vals = reinterpret_cast<const TA*>(p.vals);
-  const uint8_t* __restrict__ rows = p.rows;
-
-  for (int i = 0; i < nslabs; ++i) {
-    const int st = i % p.stages;
-    const uint32_t ph = (uint32_t)(i / p.stages) & 1u;
-    if (!mbar_wait_bounded(&full[st], ph, p.status)) return;
-    const int kbase = (s_begin + i) * p.KC;
-    const int kend = kbase + p.KC;
-    const TB* bs = Bs + st * stage_elems + lane * V;
-    while (c < c_end) {
-      const int k = __ldg(&p.col_ind[c]);
-      if (k >= kend) break;
-      TACC b[V];
-      load_b<TB, TACC, V>(bs + (size_t)(k - kbase) * NR, b);
-      const int e1 = __ldg(&p.col_start[c + 1]);
-      int e = __ldg(&p.col_start[c]);
-      // one nonzero of look-ahead hides the load latency behind the switch
-      TACC a_next = to_acc(vals[e], TACC(0));
-      int r_next = rows[e];
-      for (; e < e1; ++e) {
-        const TACC a = a_next;
-        const int r = r_next & (R - 1);
-        if (e + 1 < e1) {
-          a_next = to_acc(vals[e + 1], TACC(0));
-          r_next = rows[e + 1];
+  if constexpr (ORDER == 1) {
+    // ---- column order (Alg. 2): one B row per packed column, C row by switch
+    int c = 0, c_end = 0;
+    if (has_panel) {
+      c = __ldg(&p.panel_col[panel]);
+      c_end = __ldg(&p.panel_col[panel + 1]);
+      if (s_begin > 0) {  // first packed column of this split's K range
+        const int kb = s_begin * p.KC;
+        int lo = c, hi = c_end;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (__ldg(&p.colrec[mid].x) < kb) lo = mid + 1; else hi = mid;
         }
-        row_mac<R, V, TACC>(acc, r, a, b);
+        c = lo;
       }
-      ++c;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);
+    const RT* __restrict__ nz = reinterpret_cast<const RT*>(p.nz);
+    const int2* __restrict__ colrec = p.colrec;
+    // current column record (k = INT_MAX once the panel is exhausted)
+    int2 cur = (c < c_end) ? __ldg(&colrec[c]) : make_int2(INT_MAX, 0);
+
+    for (int i = 0; i < nslabs; ++i) {
+      const int st = i % p.stages;
+      const uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+      if (!mbar_wait_bounded(&full[st], ph, p.status)) return;
+      const int kbase = (s_begin + i) * p.KC;
+      const int kend = kbase + p.KC;
+      const TB* bs = Bs + st * stage_elems + lane * CE;
+      while (cur.x < kend) {
+        const int2 nxt = __ldg(&colrec[c + 1]);   // its start ends this column
+        TACC b[V];
+        // slab layout: [box][k_c rows][BOXW]
+        const TB* brow = bs + (size_t)(cur.x - kbase) * BOXW;
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          load_chunk<TB, TACC, CE>(brow + (size_t)((j * 32 * CE) / BOXW) * p.KC * BOXW +
+                                       (j * 32 * CE) % BOXW,
+                                   b + j * CE);
+        int e = cur.y;
+        const int e1 = nxt.y;
+        RT w = nz[e];
+        for (; e + 1 < e1; ++e) {
+          const RT w2 = nz[e + 1];   // look-ahead hides the load behind the FMAs
+          row_mac<R, V, TACC>(acc, Rec<TA>::r(w) & (R - 1), Rec<TA>::a(w), b);
+          w = w2;
+        }
+        row_mac<R, V, TACC>(acc, Rec<TA>::r(w) & (R - 1), Rec<TA>::a(w), b);
+        ++c;
+        cur = (c < c_end) ? nxt : make_int2(INT_MAX, 0);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+  } else {
+    // ---- row-slot order: register row r of C walks its own nonzeros (k
+    // ascending) and reads each one's B row from the shared slab; no run-time
+    // register indexing, rows are independent instruction streams
+    using WT = typename RowRec<TA>::T;
+    // order 3 reads the same records re-addressed by tile-list slot
+    const WT* __restrict__ rnz = reinterpret_cast<const WT*>(ORDER == 3 ? p.gnz : p.rnz);
+    int cur[R];
+    WT nxt[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t row = row0 + r;
+      int c0 = 0;
+      if (has_panel && row < p.M) {
+        c0 = __ldg(&p.rowptr[row]);
+        if (s_begin > 0) {  // first nonzero of this split's K range
+          const int kb = s_begin * p.KC;
+          int lo = c0, hi = __ldg(&p.rowptr[row + 1]) - 1;   // last entry: sentinel
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (RowRec<TA>::k(rnz[mid]) < kb) lo = mid + 1; else hi = mid;
+          }
+          c0 = lo;
+        }
+        nxt[r] = rnz[c0];
+      } else {
+        // rows past M (or no panel): point at a sentinel of this handle
+        c0 = __ldg(&p.rowptr[1]) - 1;
+        nxt[r] = rnz[c0];
+      }
+      cur[r] = c0;
+    }
+    for (int i = 0; i < nslabs; ++i) {
+      const int st = i % p.stages;
+      const uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+      if (!mbar_wait_bounded(&full[st], ph, p.status)) return;
+      const int kbase = (s_begin + i) * p.KC;
+      const int kend = kbase + p.KC;
+      const TB* bs = Bs + st * stage_elems + lane * CE;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        while (RowRec<TA>::k(nxt[r]) < kend) {
+          const WT w = nxt[r];
+          nxt[r] = rnz[++cur[r]];          // next record (the row ends on a sentinel)
+          TACC b[V];
+          const TB* brow = bs + (size_t)(RowRec<TA>::k(w) - kbase) * BOXW;
+#pragma unroll
+          for (int j = 0; j < J; ++j)
+            load_chunk<TB, TACC, CE>(brow + (size_t)((j * 32 * CE) / BOXW) * p.KC * BOXW +
+                                         (j * 32 * CE) % BOXW,
+                                     b + j * CE);
+          const TACC a = RowRec<TA>::a(w);
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[r][v] = mac(a, b[v], acc[r][v]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
   }
   if (!has_panel) return;
 
@@ -247,70 +443,94 @@ __global__ void __launch_bounds__(288, 1)
     const int64_t row = row0 + r;
     if (row >= p.M) break;
     TC* crow = C + row * p.ldc;
-    if (p.atomic_out) {
 #pragma unroll
-      for (int v = 0; v < V; ++v)
-        if (col0 + v < p.N) atomic_add_out(crow + col0 + v, out_value<TC, TACC>(acc[r][v], p, row, col0 + v));
-      continue;
-    }
-    TC o[V];
+    for (int j = 0; j < J; ++j) {
+      const int64_t col0 = n0 + j * 32 * CE + lane * CE;
+      if (col0 >= p.N) continue;
+      if (p.atomic_out) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      o[v] = (col0 + v < p.N) ? out_value<TC, TACC>(acc[r][v], p, row, col0 + v) : TC(0);
-      if (p.add_c_at_end && col0 + v < p.N) o[v] = o[v] + crow[col0 + v];
-    }
-    constexpr int OB = V * (int)sizeof(TC);
-    if (p.vec_ok && col0 + V <= p.N && (OB == 16 || OB == 8 || OB == 32)) {
-      if constexpr (OB == 32) {
-        reinterpret_cast<uint4*>(crow + col0)[0] = reinterpret_cast<uint4*>(o)[0];
-        reinterpret_cast<uint4*>(crow + col0)[1] = reinterpret_cast<uint4*>(o)[1];
-      } else if constexpr (OB == 16) {
-        *reinterpret_cast<uint4*>(crow + col0) = *reinterpret_cast<uint4*>(o);
-      } else if constexpr (OB == 8) {
-        *reinterpret_cast<uint2*>(crow + col0) = *reinterpret_cast<uint2*>(o);
+        for (int v = 0; v < CE; ++v)
+          if (col0 + v < p.N)
+            atomicAdd(crow + col0 + v, out_value<TC, TACC>(acc[r][j * CE + v], p, row, col0 + v));
+        continue;
       }
-    } else {
+      TC o[CE];
 #pragma unroll
-      for (int v = 0; v < V; ++v)
-        if (col0 + v < p.N) crow[col0 + v] = o[v];
+      for (int v = 0; v < CE; ++v) {
+        o[v] = (col0 + v < p.N) ? out_value<TC, TACC>(acc[r][j * CE + v], p, row, col0 + v)
+                                : TC(0);
+        if (p.add_c_at_end && col0 + v < p.N) o[v] = o[v] + crow[col0 + v];
+      }
+      if (p.vec_ok && col0 + CE <= p.N) {
+        store_chunk<TC, CE>(crow + col0, o);
+      } else {
+#pragma unroll
+        for (int v = 0; v < CE; ++v)
+          if (col0 + v < p.N) crow[col0 + v] = o[v];
+      }
     }
   }
 }
 
-using KernelFn = void (*)(const SparseParams, const CUtensorMap);
+using KernelFn = void (*)(const SparseParams, const CUtensorMap, const CUtensorMap);
 
 struct Entry {
   rosko_dtype a, b, c;
-  int R, V;
+  int R, V, order;
   KernelFn fn;
   size_t smem_set;
 };
 
-#define ROSKO_ENTRY(TA, TB, TC, DA, DB, DC, R, V) \
-  {DA, DB, DC, R, V, sparse_spmm_kernel<TA, TB, TC, R, V>, 0}
+#define ROSKO_COL(TA, TB, TC, DA, DB, DC, R, V) \
+  {DA, DB, DC, R, V, 1, sparse_spmm_kernel<TA, TB, TC, R, V, 1>, 0}
+#define ROSKO_ROW(TA, TB, TC, DA, DB, DC, R, V) \
+  {DA, DB, DC, R, V, 2, sparse_spmm_kernel<TA, TB, TC, R, V, 2>, 0}
+#define ROSKO_GATHER(TA, TB, TC, DA, DB, DC, R, V) \
+  {DA, DB, DC, R, V, 3, sparse_spmm_kernel<TA, TB, TC, R, V, 3>, 0}
 
+// Column order: m_r x V = 128 accumulators per lane (wide strips amortise the
+// row dispatch).  Row-slot order: 64 (its per-row cursors and look-ahead
+// records need the rest of the register file), m_r <= 16.
 Entry g_table[] = {
-    ROSKO_ENTRY(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 32, 4),
-    ROSKO_ENTRY(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 16, 8),
-    ROSKO_ENTRY(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 16, 4),
-    ROSKO_ENTRY(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 8, 8),
-    ROSKO_ENTRY(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 32, 4),
-    ROSKO_ENTRY(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 16, 8),
-    ROSKO_ENTRY(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 8, 8),
-    ROSKO_ENTRY(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 32, 4),
-    ROSKO_ENTRY(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 16, 8),
-    ROSKO_ENTRY(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 8, 8),
-    ROSKO_ENTRY(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 32, 4),
-    ROSKO_ENTRY(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 16, 8),
-    ROSKO_ENTRY(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 8, 8),
-    ROSKO_ENTRY(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 32, 2),
-    ROSKO_ENTRY(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 16, 4),
-    ROSKO_ENTRY(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 8, 4),
+    ROSKO_COL(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 32, 4),
+    ROSKO_COL(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 16, 8),
+    ROSKO_COL(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 16, 4),
+    ROSKO_COL(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 8, 16),
+    ROSKO_COL(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 8, 8),
+    ROSKO_COL(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 32, 4),
+    ROSKO_COL(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 16, 8),
+    ROSKO_COL(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 8, 16),
+    ROSKO_COL(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 8, 8),
+    ROSKO_COL(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 32, 4),
+    ROSKO_COL(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 16, 8),
+    ROSKO_COL(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 8, 16),
+    ROSKO_COL(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 32, 4),
+    ROSKO_COL(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 16, 8),
+    ROSKO_COL(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 8, 16),
+    ROSKO_COL(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 32, 2),
+    ROSKO_COL(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 16, 4),
+    ROSKO_COL(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 8, 8),
+    ROSKO_ROW(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 16, 4),
+    ROSKO_ROW(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 8, 8),
+    ROSKO_ROW(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 16, 4),
+    ROSKO_ROW(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 8, 8),
+    ROSKO_ROW(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 16, 4),
+    ROSKO_ROW(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 8, 8),
+    ROSKO_ROW(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 16, 4),
+    ROSKO_ROW(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 8, 8),
+    ROSKO_ROW(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 16, 2),
+    ROSKO_ROW(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 8, 4),
+    // row-slot with the touched-row gather: one 128-row tile (8 panels of 16)
+    ROSKO_GATHER(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 16, 4),
+    ROSKO_GATHER(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 16, 4),
+    ROSKO_GATHER(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 16, 4),
+    ROSKO_GATHER(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 16, 4),
+    ROSKO_GATHER(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 16, 2),
 };
 
-Entry* find_entry(rosko_dtype a, rosko_dtype b, rosko_dtype c, int R, int V) {
+Entry* find_entry(rosko_dtype a, rosko_dtype b, rosko_dtype c, int R, int V, int order) {
   for (auto& e : g_table)
-    if (e.a == a && e.b == b && e.c == c && e.R == R && e.V == V) return &e;
+    if (e.a == a && e.b == b && e.c == c && e.R == R && e.V == V && e.order == order) return &e;
   return nullptr;
 }
 
@@ -324,55 +544,71 @@ CUtensorMapDataType tmap_dtype(rosko_dtype d) {
 
 }  // namespace
 
-bool sparse_config_supported(rosko_dtype p_dt, rosko_dtype b_dt, rosko_dtype c_dt, int R, int V) {
-  return find_entry(p_dt, b_dt, c_dt, R, V) != nullptr;
+bool sparse_config_supported(rosko_dtype p_dt, rosko_dtype b_dt, rosko_dtype c_dt, int R, int V,
+                             int order) {
+  return find_entry(p_dt, b_dt, c_dt, R, V, order) != nullptr;
 }
 
-int sparse_default_V(rosko_dtype p_dt, int R) {
-  switch (p_dt) {
-    case ROSKO_F64: return R == 32 ? 2 : 4;
-    case ROSKO_F32: return R == 32 ? 4 : 8;
-    default: return R == 32 ? 4 : 8;
-  }
-}
-
-size_t sparse_smem_bytes(rosko_dtype b_dt, int V, int KC, int stages) {
-  return 1024 + (size_t)stages * KC * 32 * V * dtype_size(b_dt);
+// Columns per lane: column order fills 128 accumulator registers, row-slot 64
+// (FP64 accumulators take two registers each).
+int sparse_default_V(rosko_dtype p_dt, int R, int order) {
+  const int regs = (order >= 2 ? 64 : 128) / (p_dt == ROSKO_F64 ? 2 : 1);
+  return std::max(2, regs / R);
 }
 
 rosko_status sparse_spmm_launch(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N,
                                 int64_t ldb, const float* col_scale, void* C, rosko_dtype c_dt,
                                 int64_t ldc, int accumulate, const SparseLaunch& L,
+                                const int32_t* panel_list, int64_t n_panels, bool c_zeroed,
                                 cudaStream_t st) {
-  Entry* e = find_entry(h->dt, b_dt, c_dt, L.R, L.V);
+  if (n_panels <= 0) return ROSKO_OK;
+  if (L.order == 2 && !h->rnz) return ROSKO_ERR_UNSUPPORTED;
+  if (L.order == 3 && (!h->gnz || L.R != 16 || L.W != 8)) return ROSKO_ERR_UNSUPPORTED;
+  Entry* e = find_entry(h->dt, b_dt, c_dt, L.R, L.V, L.order);
   if (!e) return ROSKO_ERR_UNSUPPORTED;
   const int NR = 32 * L.V;
   const size_t bsz = dtype_size(b_dt), csz = dtype_size(c_dt);
-  const size_t smem = sparse_smem_bytes(b_dt, L.V, L.KC, L.stages);
+  const size_t smem = 1024 + (size_t)L.stages * L.KC * NR * bsz;
   if (smem > e->smem_set) {
     if (cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return ROSKO_ERR_CUDA;
     e->smem_set = smem;
   }
-
+  // a TMA box is at most 256 elements wide: wide strips take several boxes
+  const int boxes = NR > 256 ? NR / 256 : 1;
   CUtensorMap map;
   const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)h->K};
   const cuuint64_t strides[1] = {(cuuint64_t)ldb * bsz};
-  const cuuint32_t box[2] = {(cuuint32_t)NR, (cuuint32_t)L.KC};
+  const cuuint32_t box[2] = {(cuuint32_t)(NR / boxes), (cuuint32_t)L.KC};
   const cuuint32_t es[2] = {1, 1};
   CUresult r = encode_tiled(&map, tmap_dtype(b_dt), 2, const_cast<void*>(B), dims, strides, box, es,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return ROSKO_ERR_INVALID_ARG;
+  // single-row boxes for the touched-row gather
+  CUtensorMap map1 = map;
+  if (L.order == 3) {
+    const cuuint32_t box1[2] = {(cuuint32_t)(NR / boxes), 1u};
+    if (encode_tiled(&map1, tmap_dtype(b_dt), 2, const_cast<void*>(B), dims, strides, box1, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ROSKO_ERR_INVALID_ARG;
+  }
 
   SparseParams p{};
+  p.panel_list = panel_list;
+  p.n_list = n_panels;
   p.panel_col = h->panel_col;
-  p.col_ind = h->col_ind;
-  p.col_start = h->col_start;
-  p.vals = h->vals;
-  p.rows = h->rows;
+  p.colrec = h->colrec;
+  p.nz = h->nz;
+  p.rowptr = h->rowptr;
+  p.rnz = h->rnz;
+  p.gu_start = h->gu_start;
+  p.gu_k = h->gu_k;
+  p.gnz = h->gnz;
   p.row_scale = h->row_scale;
   p.col_scale = col_scale;
   p.C = C;
@@ -384,6 +620,7 @@ rosko_status sparse_spmm_launch(rosko_packed_s* h, const void* B, rosko_dtype b_
   p.KC = L.KC;
   p.stages = L.stages;
   p.split = L.split;
+  p.boxes = boxes;
   p.slabs_total = (int)((h->K + L.KC - 1) / L.KC);
   const bool dequant = (h->dt == ROSKO_I8 && c_dt == ROSKO_F32);
   p.atomic_out = L.split > 1;
@@ -393,14 +630,15 @@ rosko_status sparse_spmm_launch(rosko_packed_s* h, const void* B, rosko_dtype b_
   p.status = device_status_word();
   if (!p.status) return ROSKO_ERR_CUDA;
 
-  if (p.atomic_out && !accumulate) {
+  if (p.atomic_out && !accumulate && !c_zeroed) {
     if (cudaMemset2DAsync(C, (size_t)ldc * csz, 0, (size_t)N * csz, (size_t)h->M, st) !=
         cudaSuccess)
       return ROSKO_ERR_CUDA;
   }
-  const dim3 grid((unsigned)((h->P + L.W - 1) / L.W), (unsigned)((N + NR - 1) / NR),
-                  (unsigned)L.split);
-  e->fn<<<grid, (L.W + 1) * 32, smem, st>>>(p, map);
+  // order 3: panel_list holds 128-row tile ids and n_panels counts tiles
+  const unsigned gx = L.order == 3 ? (unsigned)n_panels : (unsigned)((n_panels + L.W - 1) / L.W);
+  const dim3 grid(gx, (unsigned)((N + NR - 1) / NR), (unsigned)L.split);
+  e->fn<<<grid, (L.W + 1) * 32, smem, st>>>(p, map, map1);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libroskogb300.so")
 
 F32, BF16, I8, F64, I32 = 0, 1, 2, 3, 4
 SCHED_ANALYTIC, SCHED_AUTOTUNE, SCHED_LEARNED, SCHED_FORCED = 0, 1, 2, 3
+ORDER_COLUMN, ORDER_ROWSLOT = 1, 2
 STATUS_NAMES = ["ROSKO_OK", "ROSKO_ERR_INVALID_ARG", "ROSKO_ERR_UNSUPPORTED", "ROSKO_ERR_OOM",
                 "ROSKO_ERR_CUDA", "ROSKO_ERR_TIMEOUT", "ROSKO_ERR_BAD_HANDLE", "ROSKO_ERR_DEVICE"]
 TORCH_TO_CODE = {torch.float32: F32, torch.bfloat16: BF16, torch.int8: I8,
@@ -36,7 +37,9 @@ class RoskoError(RuntimeError):
 class rosko_tile(ctypes.Structure):
     _fields_ = [("m_r", ctypes.c_int32), ("n_r", ctypes.c_int32), ("k_c", ctypes.c_int32),
                 ("m_c", ctypes.c_int32), ("split_k", ctypes.c_int32),
-                ("dense_split_pct", ctypes.c_int32), ("mode", ctypes.c_int32)]
+                ("dense_split_pct", ctypes.c_int32), ("dense_n_r", ctypes.c_int32),
+                ("dense_split_k", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("mode", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -75,6 +78,10 @@ def lib() -> ctypes.CDLL:
         "rosko_schedule_analytic": (ci, [i64, i64, i64, i64, i32, ci, P_tile]),
         "rosko_device_status": (ci, [ctypes.POINTER(i32), ci]),
         "rosko_kernel_launches": (i64, []),
+        "rosko_num_candidates": (i32, []),
+        "rosko_candidate": (ci, [vp, i64, i32, P_tile]),
+        "rosko_autotune": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, i32, P_tile,
+                                ctypes.POINTER(ctypes.c_float), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -136,12 +143,13 @@ def rosko_status_string(status: int) -> str:
 
 
 def rosko_pack(A: torch.Tensor, packed_dtype: int, m_r: int = 0,
-               row_scale: Optional[torch.Tensor] = None, stream=None) -> PackedA:
+               row_scale: Optional[torch.Tensor] = None, stream=None,
+               dense_min_pct: int = 0) -> PackedA:
     """Alg. 1 on the device: pack the dense row-major A (F32, BF16 or I8)."""
     L = lib()
     M, K = A.shape
     lda = _ld(A) if A.numel() else max(K, 1)
-    tile = make_tile(m_r=m_r)
+    tile = make_tile(m_r=m_r, dense_split_pct=dense_min_pct)
     out = ctypes.c_void_p()
     st = L.rosko_pack(_ptr(A) if A.numel() else None, TORCH_TO_CODE[A.dtype], M, K, lda,
                       int(packed_dtype), _ptr(row_scale), ctypes.byref(tile),
@@ -222,3 +230,31 @@ def rosko_device_status(clear: bool = False) -> int:
 
 def rosko_kernel_launches() -> int:
     return int(lib().rosko_kernel_launches())
+
+
+def rosko_num_candidates() -> int:
+    return int(lib().rosko_num_candidates())
+
+
+def rosko_candidate(A: PackedA, N: int, index: int):
+    """Candidate schedule `index` as a forced tile, or None if it does not apply."""
+    t = rosko_tile()
+    st = lib().rosko_candidate(A.handle, N, index, ctypes.byref(t))
+    if st == 2:
+        return None
+    _check(st, "rosko_candidate")
+    return t
+
+
+def rosko_autotune(A: PackedA, B: torch.Tensor, C: torch.Tensor,
+                   col_scale: Optional[torch.Tensor] = None, reps: int = 3, stream=None):
+    """Time every candidate; returns (best tile, list of per-candidate ms or None)."""
+    K, N = B.shape
+    nc = rosko_num_candidates()
+    times = (ctypes.c_float * nc)()
+    best = rosko_tile()
+    st = lib().rosko_autotune(A.handle, _ptr(B), TORCH_TO_CODE[B.dtype], N, _ld(B),
+                              _ptr(col_scale), _ptr(C), TORCH_TO_CODE[C.dtype], _ld(C), reps,
+                              ctypes.byref(best), times, ctypes.c_void_p(_stream(stream)))
+    _check(st, "rosko_autotune")
+    return best, [None if t < 0 else float(t) for t in times]

@@ -1,0 +1,99 @@
+"""Tensor-core dense-panel path (tcgen05, BF16 in / FP32 accumulate) and the
+sparse/dense split, against the FP64 oracle on the BF16-rounded inputs
+(normalised error <= 1e-5).  GPU only."""
+import numpy as np
+import pytest
+import torch
+
+from tests._lib import built
+from tests.test_gpu_spmm import _ldpad
+from oracle.spmm import spmm, normalized_error
+from oracle.quant import bf16_round
+from paper_2307_03930_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(rosko, A, B, tile, rows=None, accumulate=False, C0=None, dense_min_pct=0):
+    M, K = A.shape
+    N = B.shape[1]
+    h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16, dense_min_pct=dense_min_pct)
+    Bd = _ldpad(torch.from_numpy(B).to(torch.bfloat16), 2)
+    C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    if C0 is not None:
+        C.copy_(torch.from_numpy(C0))
+    l0 = rosko.rosko_kernel_launches()
+    rosko.rosko_spmm(h, Bd, C, tile=tile, accumulate=accumulate)
+    launches = rosko.rosko_kernel_launches() - l0
+    torch.cuda.synchronize()
+    assert rosko.rosko_device_status(clear=True) == 0
+    rows = np.arange(M) if rows is None else np.asarray(rows)
+    ref, D = spmm(bf16_round(A), bf16_round(B), rows=rows, C0=C0)
+    if C0 is not None:
+        D = D + np.abs(C0[rows].astype(np.float64))
+    err = normalized_error(C.cpu().numpy()[rows], ref, D)
+    return err, launches
+
+
+@pytest.mark.parametrize("M,K,N", [(128, 64, 128), (130, 77, 257), (256, 1000, 300),
+                                   (1, 8, 1), (300, 129, 64), (384, 2048, 520)])
+@pytest.mark.parametrize("TN,ctas", [(128, 0), (256, 0), (256, 7), (128, 1), (256, 3)])
+def test_all_dense(M, K, N, TN, ctas):
+    # stream-K over `ctas` CTAs (0: one per SM): tiles whose K range is cut
+    # between CTAs are added with atomics, whole tiles are stored
+    rosko = built()
+    A = gen.sparse_weight(M, K, 0.5, gen.rng_for(7, M, K), "uniform")
+    B = gen.normal((K, N), gen.rng_for(8, K, N))
+    t = rosko.make_tile(dense_split_pct=1, dense_n_r=TN, dense_split_k=ctas)
+    err, launches = _run(rosko, A, B, t)
+    assert err <= 1e-5, err
+    assert launches == 1          # only the tensor-core kernel ran
+
+
+def test_mixed_split_powerlaw():
+    # power-law rows give tiles of very different density: some run dense,
+    # the others on the sparse kernel, in one call
+    rosko = built()
+    A = gen.sparse_weight(1000, 700, 0.97, gen.rng_for(9), "powerlaw")
+    B = gen.relu_normal((700, 333), gen.rng_for(10))
+    h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16)
+    t = rosko.make_tile(dense_split_pct=3)
+    err, launches = _run(rosko, A, B, t)
+    assert err <= 1e-5, err
+    dens = [(A[i:i + 128] != 0).mean() for i in range(0, 1000, 128)]
+    n_dense = sum(d * 100 >= 3 for d in dens)
+    assert 0 < n_dense < len(dens)
+    assert launches == 2
+
+
+@pytest.mark.parametrize("ctas", [1, 5, 0])
+def test_dense_accumulate(ctas):
+    rosko = built()
+    A = gen.sparse_weight(200, 512, 0.8, gen.rng_for(11), "uniform")
+    B = gen.normal((512, 200), gen.rng_for(12))
+    C0 = np.random.default_rng(3).standard_normal((200, 200)).astype(np.float32)
+    t = rosko.make_tile(dense_split_pct=1, dense_split_k=ctas)
+    err, _ = _run(rosko, A, B, t, accumulate=True, C0=C0)
+    assert err <= 1e-5, err
+
+
+def test_no_copy_means_sparse_only():
+    rosko = built()
+    A = gen.sparse_weight(256, 300, 0.5, gen.rng_for(13), "uniform")
+    B = gen.normal((300, 100), gen.rng_for(14))
+    t = rosko.make_tile(dense_split_pct=1)
+    err, launches = _run(rosko, A, B, t, dense_min_pct=101)
+    assert err <= 1e-5 and launches == 1
+
+
+@pytest.mark.parametrize("s", [0.5, 0.9, 0.95])
+def test_c2_dense_full_size_sampled(s):
+    # the bench's launch configuration: analytic schedule (dense split at 3%)
+    rosko = built()
+    rng = gen.rng_for(1, int(round(s * 1000)))
+    A = gen.magnitude_prune(gen.normal((512, 4608), rng), s)
+    B = gen.relu_normal((4608, 3136), rng)
+    rows = np.random.default_rng(int(s * 1000)).choice(512, 40, replace=False)
+    err, launches = _run(rosko, A, B, None, rows=rows)
+    assert err <= 1e-5, err
+    assert launches == 1

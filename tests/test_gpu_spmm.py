@@ -103,17 +103,25 @@ SHAPES = [(1, 1, 1, 0.0), (33, 17, 65, 0.5), (70, 300, 129, 0.9), (200, 1000, 30
 
 @pytest.mark.parametrize("mode", ["f32", "bf16", "i8", "i8f", "f64"])
 @pytest.mark.parametrize("M,K,N,s", SHAPES)
-def test_small_ragged(mode, M, K, N, s):
+@pytest.mark.parametrize("m_r", [0, 32])
+def test_small_ragged(mode, M, K, N, s, m_r):
+    # m_r = 0: the library's density-based panel height (8 or 16)
     rosko = built()
     A, B = _problem(M, K, N, s, seed=0)
-    m_r = 16 if mode == "f64" else 32
+    if mode == "f64" and m_r == 32:
+        m_r = 16
     check(mode, *run(rosko, A, B, mode, m_r=m_r))
 
 
-# every compiled (m_r, V) variant with several CTA heights, slabs and K splits
-VARIANTS = {"f32": [(32, 4), (16, 8), (16, 4), (8, 8)], "bf16": [(32, 4), (16, 8), (8, 8)],
-            "i8": [(32, 4), (16, 8), (8, 8)], "i8f": [(32, 4), (16, 8), (8, 8)],
-            "f64": [(32, 2), (16, 4), (8, 4)]}
+# every compiled (order, m_r, V) variant with several CTA heights, slabs and K
+# splits; order 1 = column order (Alg. 2), order 2 = row-slot order
+VARIANTS = {"f32": [(1, 32, 4), (1, 16, 8), (1, 16, 4), (1, 8, 16), (1, 8, 8), (2, 16, 4),
+                    (2, 8, 8), (3, 16, 4)],
+            "bf16": [(1, 32, 4), (1, 16, 8), (1, 8, 16), (1, 8, 8), (2, 16, 4), (2, 8, 8),
+                     (3, 16, 4)],
+            "i8": [(1, 32, 4), (1, 16, 8), (1, 8, 16), (2, 16, 4), (2, 8, 8), (3, 16, 4)],
+            "i8f": [(1, 32, 4), (1, 16, 8), (1, 8, 16), (2, 16, 4), (2, 8, 8), (3, 16, 4)],
+            "f64": [(1, 32, 2), (1, 16, 4), (1, 8, 8), (2, 16, 2), (2, 8, 4), (3, 16, 2)]}
 
 
 @pytest.mark.parametrize("mode", list(VARIANTS))
@@ -122,8 +130,9 @@ def test_forced_tiles(mode, W, KC, split):
     rosko = built()
     A, B = _problem(150, 700, 300, 0.8, seed=1)
     esz = {"f32": 4, "bf16": 2, "i8": 1, "i8f": 1, "f64": 4}[mode]
-    for R, V in VARIANTS[mode]:
-        t = rosko.make_tile(m_r=R, n_r=32 * V, k_c=KC, m_c=W * R, split_k=split,
+    for order, R, V in VARIANTS[mode]:
+        m_c = 128 if order == 3 else W * R   # order 3: one CTA per 128-row tile
+        t = rosko.make_tile(m_r=R, n_r=32 * V, k_c=KC, m_c=m_c, split_k=split, order=order,
                             mode=rosko.SCHED_FORCED)
         if 2 * KC * 32 * V * esz > 200 * 1024:
             # a two-slab ring would not fit in shared memory: rejected on the host
@@ -132,6 +141,16 @@ def test_forced_tiles(mode, W, KC, split):
             assert ei.value.status == 1
             continue
         check(mode, *run(rosko, A, B, mode, m_r=R, tile=t))
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("s", [0.0, 0.99, 0.999])
+def test_orders_agree_bitwise_int8(order, s):
+    # integer accumulation is exact: both traversals give the same INT32 C
+    rosko = built()
+    A, B = _problem(96, 333, 150, s, seed=21)
+    t = rosko.make_tile(order=order)
+    check("i8", *run(rosko, A, B, "i8", m_r=16, tile=t))
 
 
 @pytest.mark.parametrize("mode", ["f32", "bf16", "i8", "i8f", "f64"])
@@ -145,9 +164,9 @@ def test_accumulate_in_place(mode, split):
         C0 = rng.integers(-1000, 1000, size=(90, 200)).astype(np.int32)
     else:
         C0 = rng.standard_normal((90, 200)).astype(np.float64 if mode == "f64" else np.float32)
-    m_r = 16 if mode == "f64" else 32
-    t = rosko.make_tile(split_k=split)
-    check(mode, *run(rosko, A, B, mode, m_r=m_r, tile=t, accumulate=True, C0=C0))
+    for order, m_r in ((1, 16 if mode == "f64" else 32), (2, 16), (3, 16)):
+        t = rosko.make_tile(split_k=split, order=order)
+        check(mode, *run(rosko, A, B, mode, m_r=m_r, tile=t, accumulate=True, C0=C0))
 
 
 def test_identity_and_zero():
@@ -192,3 +211,15 @@ def test_c2_full_size_sampled(s, mode):
     B = gen.relu_normal((4608, 3136), rng)
     rows = np.random.default_rng(int(s * 1000)).choice(512, 48, replace=False)
     check(mode, *run(rosko, A, B, mode, rows=rows))
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16", "i8"])
+def test_gather_empty_tiles_and_ragged(mode):
+    # tiles whose rows are all zero have an empty touched-column list; the
+    # last tile is ragged (M = 300)
+    rosko = built()
+    A, B = _problem(300, 777, 130, 0.995, seed=31)
+    A[0:128] = 0                       # tile 0: nothing touched
+    A[256:300, :5] = 1.0               # ragged tile 2: a few dense columns
+    t = rosko.make_tile(order=3)
+    check(mode, *run(rosko, A, B, mode, m_r=16, tile=t))

@@ -381,7 +381,7 @@ def profile_case(args, rosko, torch):
     out = {"sparsity": SPARSITIES[i]}
     forms = (("bf16", rosko.BF16, torch.bfloat16, None),
              ("bf16_colorder", rosko.BF16, torch.bfloat16, rosko.make_tile(order=1)),
-             ("bf16_sparse_only", rosko.BF16, torch.bfloat16, rosko.make_tile(dense_split_pct=101)),
+             ("bf16_sparse_only", rosko.BF16, torch.bfloat16, rosko.make_tile(dense_split_pm=1001)),
              ("f32", rosko.F32, torch.float32, None),
              ("f32_colorder", rosko.F32, torch.float32, rosko.make_tile(order=1)))
     for name, code, bd, tile in forms:

@@ -76,10 +76,11 @@ typedef enum {
  *   k_c   rows of B staged in shared memory per pipeline slab.
  *   m_c   C rows per CTA = warps per CTA x m_r.
  *   split_k  number of K ranges reduced into C with atomics (>= 1).
- *   dense_split_pct  BF16 only: 128-row tiles of A whose density in percent
- *         is >= this value run on the tensor-core dense-panel path, the
- *         others on the sparse path; >= 101 = never.  At pack time the same
- *         field is the minimum density for which a dense copy is kept.
+ *   dense_split_pm  BF16 only: 128-row tiles of A whose density in per mille
+ *         (nonzeros per 1000 entries) is >= this value run on the tensor-core
+ *         dense-panel path, the others on the sparse path; >= 1001 = never.
+ *         At pack time the same field is the minimum density for which a
+ *         dense copy is kept.
  *   dense_n_r      C columns per tensor-core CTA tile (128 or 256).
  *   dense_split_k  CTAs over which the stream-K tensor-core path divides its
  *         (tile, K slab) work (default: one per SM); a tile whose K range
@@ -103,7 +104,7 @@ typedef struct {
   int32_t k_c;
   int32_t m_c;
   int32_t split_k;
-  int32_t dense_split_pct;
+  int32_t dense_split_pm;
   int32_t dense_n_r;
   int32_t dense_split_k;
   int32_t order;
@@ -125,8 +126,9 @@ const char* rosko_status_string(rosko_status s);
  *                (row_scale_dev gives the scales, NULL = all 1);
  *           F64  from F32 (exact widening; FP64 check mode).
  * row_scale_dev  I8-from-I8 only: M FP32 row scales (device), else NULL.
- * tile    only tile->m_r and, for BF16, tile->dense_split_pct (minimum tile
- *         density, in percent, for keeping a dense copy; <= 0: 1%) are read.
+ * tile    only tile->m_r and, for BF16, tile->dense_split_pm (minimum tile
+ *         density, per mille, for keeping a dense copy; <= 0: 1 per mille)
+ *         are read.
  *         m_r <= 0: 16.
  * out     receives the new handle (set to NULL on error).
  * Zero test: IEEE a != 0, so -0.0 is dropped and NaN/Inf are kept.
@@ -229,6 +231,59 @@ rosko_status rosko_autotune(rosko_packed_t A, const void* B_dev, rosko_dtype b_d
                             int64_t ldb, const float* col_scale_dev, void* C_dev,
                             rosko_dtype c_dtype, int64_t ldc, int32_t reps, rosko_tile* best,
                             float* times_ms, rosko_stream_t stream);
+
+/*
+ * rosko_time_tile - mean device time in ms of rosko_spmm(A, B, C) with `tile`
+ * (NULL = analytic rule): `reps` launches, each after an L2 flush, captured
+ * as one CUDA graph (host launch overhead excluded), minus the flushes.
+ * C is overwritten.  Synchronises.
+ */
+rosko_status rosko_time_tile(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                             int64_t ldb, const float* col_scale_dev, void* C_dev,
+                             rosko_dtype c_dtype, int64_t ldc, const rosko_tile* tile,
+                             int32_t reps, float* ms, rosko_stream_t stream);
+
+/*
+ * Learned schedule selector.  Features (16, double) of a packed A and a
+ * width N: log2 M, log2 K, log2 N, density, log2(1+nnz), log2(1+mean row
+ * nnz), row-nnz coefficient of variation, log2(1+max row nnz) - log2(1+mean),
+ * fractions of rows in four row-density bins (100 r < K, 20 r < K <= 100 r,
+ * 5 r < K <= 20 r, K <= 5 r for row nnz r), mean fraction of non-empty
+ * columns per panel, panel-nnz coefficient of variation, log2(1 + nnz per
+ * packed column), fraction of empty panels.  Synchronises.
+ */
+rosko_status rosko_features(rosko_packed_t A, int64_t N, double* features16, rosko_stream_t stream);
+
+/*
+ * The selector network: n_in -> 64 -> 64 -> 64 -> n_out, ReLU on the hidden
+ * layers, FP32.  Parameters are one flat device array, per layer the weight
+ * matrix [out][in] row-major followed by the bias [out].
+ */
+int64_t rosko_mlp_param_count(int32_t n_in, int32_t n_out);
+/* Workspace (floats) rosko_mlp_loss_grad needs for `batch` samples. */
+int64_t rosko_mlp_workspace_floats(int64_t batch, int32_t n_out);
+/* logits_dev[batch x n_out] = MLP(X_dev[batch x n_in]); acts_dev holds
+ * 3 x batch x 64 floats of hidden activations (device, caller-owned). */
+rosko_status rosko_mlp_forward(const float* params_dev, const float* X_dev, int64_t batch,
+                               int32_t n_in, int32_t n_out, float* acts_dev, float* logits_dev,
+                               rosko_stream_t stream);
+/* Mean softmax cross-entropy of the batch against target rows Y_dev
+ * [batch x n_out] (one-hot or soft) into *loss_dev, and its gradient with
+ * respect to every parameter into grads_dev (same layout as params). */
+rosko_status rosko_mlp_loss_grad(const float* params_dev, const float* X_dev, const float* Y_dev,
+                                 int64_t batch, int32_t n_in, int32_t n_out, float* grads_dev,
+                                 float* loss_dev, float* workspace_dev, rosko_stream_t stream);
+/* One Adam step (bias-corrected, step >= 1) on n parameters in place. */
+rosko_status rosko_mlp_adam(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev,
+                            int64_t n, int32_t step, float lr, float beta1, float beta2,
+                            float eps, rosko_stream_t stream);
+/* Install trained selector weights (host array, n_in = 16, n_out =
+ * rosko_num_candidates()) with the feature standardisation (mean, std) and
+ * the training range [lo, hi] per feature; ROSKO_SCHED_LEARNED then picks the
+ * candidate with the largest logit, or the analytic rule for features
+ * outside the range. */
+rosko_status rosko_selector_set(const float* params_host, int64_t n_params, const double* mean16,
+                                const double* std16, const double* lo16, const double* hi16);
 
 /*
  * rosko_device_status - read (and with clear != 0, reset) the current

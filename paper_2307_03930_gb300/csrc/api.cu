@@ -98,19 +98,6 @@ CUresult encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank,
   return g_encode(map, dt, rank, gaddr, dims, strides, box, estrides, il, sw, l2, oob);
 }
 
-// ---------------------------------------------------------------------------
-// Analytic schedule: Sec. 4.2 re-derived for one GB300.
-//
-// Register level (Eq. 3 analog): a warp keeps an m_r x 32V C tile in
-// registers; each staged B element is reused d*m_r times, so m_r is as large
-// as the register file allows (m_r * V accumulators <= 128 per lane).
-// Shared-memory level (Eq. 1 analog, per SM instead of per core): the ring of
-// `stages` k_c x n_r B slabs must leave room for two CTAs per SM
-// (<= ~100 KB each) so that one CTA's epilogue overlaps another's stream.
-// Chip level (Eq. 2 analog): B is re-read from L2 once per CTA row group,
-// ceil(M / m_c) times, so m_c = W m_r grows with M; K is split only as far as
-// needed to put ~2 CTAs on every SM.
-// ---------------------------------------------------------------------------
 // Tensor-core dense-panel tiles: the stream-K kernel spreads the work over one
 // CTA per SM whatever the tile count, so only the CTA width matters: 256 halves
 // the L2->SM traffic of A (read once per column tile) against 128.
@@ -121,14 +108,17 @@ void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, i
   *ctas_out = sms;
 }
 
-// Density (in percent) from which a 128-row tile runs on the tensor cores.
+// Density (per mille) from which a 128-row tile runs on the tensor cores.
 // Sec. 4.2 balances work against bandwidth; here the balance is between two
 // engines: a dense tile costs 2*128*K*N tensor-core flops, its sparse form
-// 2*nnz*N CUDA-core flops.  With ~1.6 PFLOP/s (BF16 dense, measured) against
-// an effective ~35 TFLOP/s for the row-skipping kernel the break-even density
-// is ~2%; 3% leaves margin for the tensor path's B reads at high sparsity.
-constexpr int kDenseSplitPct = 3;
-constexpr int kDenseCopyPct = 1;
+// 2*nnz*N CUDA-core flops, so the break-even density is the ratio of the
+// two engines' effective rates.  Measured on GB300 for a 512 x 4608 x 3136
+// layer: ~460 TFLOP/s of dense work for the stream-K tcgen05 kernel against
+// ~2-3 TFLOP/s effective for the row-skipping kernel at 99% sparsity, so the
+// break-even sits near 5 per mille (the autotuner and the selector refine it
+// per shape).
+constexpr int kDenseSplitPm = 5;
+constexpr int kDenseCopyPm = 1;
 
 // ---------------------------------------------------------------------------
 // Analytic schedule: Sec. 4.2 re-derived for one GB300.
@@ -176,7 +166,7 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
   t->k_c = KC;
   t->m_c = W * m_r;
   t->split_k = (int32_t)split;
-  t->dense_split_pct = (dt == ROSKO_BF16) ? kDenseSplitPct : 101;
+  t->dense_split_pm = (dt == ROSKO_BF16) ? kDenseSplitPm : 1001;
   int TN = 256, ds = 1;
   dense_config((M + 127) / 128, N, K, sms, &TN, &ds);
   t->dense_n_r = TN;
@@ -234,8 +224,8 @@ rosko_status rosko_pack(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64
   }
   const int64_t P = (M + m_r - 1) / m_r;
   if (P > 65535) return ROSKO_ERR_INVALID_ARG;
-  const int32_t dense_min = (tile && tile->dense_split_pct > 0) ? tile->dense_split_pct
-                                                                 : kDenseCopyPct;
+  const int32_t dense_min = (tile && tile->dense_split_pm > 0) ? tile->dense_split_pm
+                                                                 : kDenseCopyPm;
   rosko_packed_s* h = nullptr;
   rosko_status s = pack_impl(A_dev, a_dtype, M, K, lda, packed_dtype, row_scale_dev, m_r,
                              dense_min, static_cast<cudaStream_t>(stream), &h);
@@ -331,16 +321,16 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
     if (tile->k_c > 0) t.k_c = tile->k_c;
     if (tile->m_c > 0) t.m_c = tile->m_c;
     if (tile->split_k > 0) t.split_k = tile->split_k;
-    if (tile->dense_split_pct > 0) t.dense_split_pct = tile->dense_split_pct;
+    if (tile->dense_split_pm > 0) t.dense_split_pm = tile->dense_split_pm;
     if (tile->dense_n_r > 0) t.dense_n_r = tile->dense_n_r;
     if (tile->dense_split_k > 0) t.dense_split_k = tile->dense_split_k;
     if (tile->order > 0) t.order = tile->order;
   }
   // ---- dense-panel split: a prefix of the density-sorted dense copies ----
   int64_t n_dense = 0, dense_panels = 0;
-  if (p == ROSKO_BF16 && A->n_copy > 0 && t.dense_split_pct <= 100) {
+  if (p == ROSKO_BF16 && A->n_copy > 0 && t.dense_split_pm <= 1000) {
     while (n_dense < A->n_copy &&
-           A->tile_density[(size_t)n_dense] * 100.0 >= (double)t.dense_split_pct) {
+           A->tile_density[(size_t)n_dense] * 1000.0 >= (double)t.dense_split_pm) {
       dense_panels += A->tile_panels[(size_t)A->tile_order[(size_t)n_dense]];
       ++n_dense;
     }
@@ -592,6 +582,77 @@ rosko_status rosko_autotune(rosko_packed_t A, const void* B_dev, rosko_dtype b_d
   std::lock_guard<std::mutex> lk(A->mu);
   A->sched_cache[N * 4 + ROSKO_SCHED_AUTOTUNE] = *best;
   return ROSKO_OK;
+}
+
+rosko_status rosko_time_tile(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                             int64_t ldb, const float* col_scale_dev, void* C_dev,
+                             rosko_dtype c_dtype, int64_t ldc, const rosko_tile* tile,
+                             int32_t reps, float* ms, rosko_stream_t stream) {
+  if (!ms) return ROSKO_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  bool done = false;
+  rosko_status v = spmm_validate(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, 0,
+                                 st, &done);
+  if (v != ROSKO_OK) return v;
+  if (done) {
+    *ms = 0.0f;
+    return ROSKO_OK;
+  }
+  rosko_status err = ROSKO_OK;
+  *ms = time_tile(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, tile, reps, st,
+                  &err);
+  return err;
+}
+
+rosko_status rosko_features(rosko_packed_t A, int64_t N, double* features16,
+                            rosko_stream_t stream) {
+  if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
+  if (!features16 || N < 1) return ROSKO_ERR_INVALID_ARG;
+  return features_impl(A, N, features16, static_cast<cudaStream_t>(stream));
+}
+
+int64_t rosko_mlp_param_count(int32_t n_in, int32_t n_out) {
+  if (n_in < 1 || n_out < 1) return 0;
+  return mlp_param_count(n_in, n_out);
+}
+
+int64_t rosko_mlp_workspace_floats(int64_t batch, int32_t n_out) {
+  if (batch < 1 || n_out < 1) return 0;
+  return mlp_workspace_floats(batch, n_out);
+}
+
+rosko_status rosko_mlp_forward(const float* params_dev, const float* X_dev, int64_t batch,
+                               int32_t n_in, int32_t n_out, float* acts_dev, float* logits_dev,
+                               rosko_stream_t stream) {
+  if (!params_dev || !X_dev || !acts_dev || !logits_dev || batch < 1 || n_in < 1 || n_out < 1)
+    return ROSKO_ERR_INVALID_ARG;
+  return mlp_forward(params_dev, X_dev, batch, n_in, n_out, acts_dev, logits_dev,
+                     static_cast<cudaStream_t>(stream));
+}
+
+rosko_status rosko_mlp_loss_grad(const float* params_dev, const float* X_dev, const float* Y_dev,
+                                 int64_t batch, int32_t n_in, int32_t n_out, float* grads_dev,
+                                 float* loss_dev, float* workspace_dev, rosko_stream_t stream) {
+  if (!params_dev || !X_dev || !Y_dev || !grads_dev || !loss_dev || !workspace_dev ||
+      batch < 1 || n_in < 1 || n_out < 1)
+    return ROSKO_ERR_INVALID_ARG;
+  return mlp_loss_grad(params_dev, X_dev, Y_dev, batch, n_in, n_out, grads_dev, loss_dev,
+                       workspace_dev, static_cast<cudaStream_t>(stream));
+}
+
+rosko_status rosko_mlp_adam(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev,
+                            int64_t n, int32_t step, float lr, float beta1, float beta2,
+                            float eps, rosko_stream_t stream) {
+  if (!params_dev || !grads_dev || !m_dev || !v_dev || n < 1 || step < 1)
+    return ROSKO_ERR_INVALID_ARG;
+  return mlp_adam(params_dev, grads_dev, m_dev, v_dev, n, step, lr, beta1, beta2, eps,
+                  static_cast<cudaStream_t>(stream));
+}
+
+rosko_status rosko_selector_set(const float* params_host, int64_t n_params, const double* mean16,
+                                const double* std16, const double* lo16, const double* hi16) {
+  if (!params_host || !mean16 || !std16 || !lo16 || !hi16) return ROSKO_ERR_INVALID_ARG;
+  return selector_set(params_host, (int)n_params, num_candidates(), mean16, std16, lo16, hi16);
 }
 
 int64_t rosko_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -27,9 +27,9 @@ const SparseCand kSparse[] = {
     {1, 4, 64, 1}, {1, 8, 32, 4},
 };
 constexpr int kNumSparse = sizeof(kSparse) / sizeof(kSparse[0]);
-// Dense-split thresholds in percent (101 = never).
-const int kDensePct[] = {101, 2, 5, 12};
-constexpr int kNumDense = sizeof(kDensePct) / sizeof(kDensePct[0]);
+// Dense-split thresholds in per mille (1001 = never).
+const int kDensePm[] = {1001, 1, 5, 20, 60};
+constexpr int kNumDense = sizeof(kDensePm) / sizeof(kDensePm[0]);
 
 }  // namespace
 
@@ -41,10 +41,10 @@ bool candidate_tile(const rosko_packed_s* h, int64_t N, int idx, rosko_tile* t) 
   (void)N;
   if (idx < 0 || idx >= num_candidates()) return false;
   const SparseCand& sc = kSparse[idx / kNumDense];
-  const int dpct = kDensePct[idx % kNumDense];
+  const int dpct = kDensePm[idx % kNumDense];
   if (sc.order == 3 && (!h->gnz || h->m_r != 16)) return false;
   if (sc.order == 2 && !h->rnz) return false;
-  if (dpct <= 100 && !(h->dt == ROSKO_BF16 && h->n_copy > 0)) return false;
+  if (dpct <= 1000 && !(h->dt == ROSKO_BF16 && h->n_copy > 0)) return false;
   const int V = sparse_default_V(h->dt, h->m_r, sc.order);
   const int W = sc.order == 3 ? 128 / h->m_r : sc.W;
   const size_t esz = h->dt == ROSKO_F64 ? 4 : dtype_size(h->dt);
@@ -55,7 +55,7 @@ bool candidate_tile(const rosko_packed_s* h, int64_t N, int idx, rosko_tile* t) 
   t->k_c = sc.KC;
   t->m_c = W * h->m_r;
   t->split_k = sc.split;
-  t->dense_split_pct = dpct;
+  t->dense_split_pm = dpct;
   t->order = sc.order;
   t->mode = ROSKO_SCHED_FORCED;
   return true;
@@ -141,6 +141,31 @@ static float time_candidate(rosko_packed_s* h, const void* B, rosko_dtype b_dt, 
     if (*err != ROSKO_OK) return -1.0f;
   }
   return std::max(result[0] - result[1], 1e-4f);
+}
+
+float time_tile(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N, int64_t ldb,
+                const float* col_scale, void* C, rosko_dtype c_dt, int64_t ldc,
+                const rosko_tile* t, int reps, cudaStream_t st, rosko_status* err) {
+  *err = ROSKO_OK;
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    *err = ROSKO_ERR_CUDA;
+    return -1.0f;
+  }
+  cudaStream_t ts;
+  cudaEvent_t e0, e1;
+  if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess) {
+    *err = ROSKO_ERR_CUDA;
+    return -1.0f;
+  }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const float ms = time_candidate(h, B, b_dt, N, ldb, col_scale, C, c_dt, ldc, t,
+                                  reps < 1 ? 3 : reps, ts, e0, e1, err);
+  cudaStreamSynchronize(ts);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(ts);
+  return ms;
 }
 
 rosko_status autotune_impl(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N,

@@ -100,7 +100,7 @@ inline bool handle_ok(const rosko_packed_s* h) { return h && h->magic == kHandle
 constexpr int kDenseTileRows = 128;
 rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
                        rosko_dtype p_dt, const float* row_scale_in, int32_t m_r,
-                       int32_t dense_min_pct, cudaStream_t stream, rosko_packed_s** out);
+                       int32_t dense_min_pm, cudaStream_t stream, rosko_packed_s** out);
 rosko_status unpack_impl(rosko_packed_s* h, void* A_out, int64_t lda, cudaStream_t stream);
 rosko_status count_nonzeros(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
                             cudaStream_t st, int64_t* out);
@@ -154,4 +154,19 @@ rosko_status autotune_impl(rosko_packed_s* h, const void* B, rosko_dtype b_dt, i
 
 // selector.cu
 rosko_status select_learned(rosko_packed_s* h, int64_t N, rosko_tile* out, cudaStream_t st);
+rosko_status features_impl(rosko_packed_s* h, int64_t N, double* f, cudaStream_t st);
+int64_t mlp_param_count(int n_in, int n_out);
+int64_t mlp_workspace_floats(int64_t batch, int n_out);
+rosko_status mlp_forward(const float* params, const float* X, int64_t batch, int n_in, int n_out,
+                         float* acts, float* logits, cudaStream_t st);
+rosko_status mlp_loss_grad(const float* params, const float* X, const float* Y, int64_t batch,
+                           int n_in, int n_out, float* grads, float* loss, float* ws,
+                           cudaStream_t st);
+rosko_status mlp_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
+                      float b1, float b2, float eps, cudaStream_t st);
+rosko_status selector_set(const float* params, int n_params, int n_out, const double* mean,
+                          const double* stdv, const double* lo, const double* hi);
+float time_tile(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N, int64_t ldb,
+                const float* col_scale, void* C, rosko_dtype c_dt, int64_t ldc,
+                const rosko_tile* t, int reps, cudaStream_t st, rosko_status* err);
 }  // namespace rosko

@@ -654,7 +654,7 @@ rosko_status build_row_stream(const S* A, int64_t lda, const float* scale, rosko
 
 // Dense-panel split bookkeeping and dense copies (BF16 packs only).
 template <class S>
-rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pct, rosko_packed_s* h,
+rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pm, rosko_packed_s* h,
                                cudaStream_t st) {
   const int64_t M = h->M, K = h->K, P = h->P;
   if (M == 0 || K == 0) return ROSKO_OK;
@@ -681,7 +681,7 @@ rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pct, r
   int64_t n_copy = 0;
   for (int64_t c = 0; c < T; ++c) {
     h->tile_density[(size_t)c] = dens[(size_t)h->tile_order[(size_t)c]];
-    if (h->tile_density[(size_t)c] * 100.0 >= (double)dense_min_pct) n_copy = c + 1;
+    if (h->tile_density[(size_t)c] * 1000.0 >= (double)dense_min_pm) n_copy = c + 1;
   }
   std::vector<int32_t> panel_order;
   panel_order.reserve((size_t)P);
@@ -724,7 +724,7 @@ rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pct, r
 
 rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
                        rosko_dtype p_dt, const float* row_scale_in, int32_t m_r,
-                       int32_t dense_min_pct, cudaStream_t stream, rosko_packed_s** out) {
+                       int32_t dense_min_pm, cudaStream_t stream, rosko_packed_s** out) {
   rosko_packed_s* h = new (std::nothrow) rosko_packed_s();
   if (!h) return ROSKO_ERR_OOM;
   cudaGetDevice(&h->device);
@@ -747,11 +747,11 @@ rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, in
                                                  false, h, stream);
   else if (a_dt == ROSKO_I8 && p_dt == ROSKO_I8)
     s = pack_typed<int8_t, int8_t>((const int8_t*)A, M, K, lda, row_scale_in, false, h, stream);
-  if (s == ROSKO_OK && p_dt == ROSKO_BF16 && dense_min_pct <= 100) {
+  if (s == ROSKO_OK && p_dt == ROSKO_BF16 && dense_min_pm <= 1000) {
     if (a_dt == ROSKO_F32)
-      s = build_dense_tiles<float>((const float*)A, lda, dense_min_pct, h, stream);
+      s = build_dense_tiles<float>((const float*)A, lda, dense_min_pm, h, stream);
     else
-      s = build_dense_tiles<__nv_bfloat16>((const __nv_bfloat16*)A, lda, dense_min_pct, h,
+      s = build_dense_tiles<__nv_bfloat16>((const __nv_bfloat16*)A, lda, dense_min_pm, h,
                                            stream);
   }
   if (s != ROSKO_OK) {

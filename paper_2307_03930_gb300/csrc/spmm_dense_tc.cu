@@ -20,6 +20,7 @@
 // between CTAs is added into C with 16-byte atomics; a tile owned whole is
 // stored.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "handle.hpp"
@@ -32,15 +33,28 @@ constexpr int kTM = 128;             // rows of a dense tile (MMA M)
 constexpr int kTK = 64;              // K per stage: 64 BF16 = one 128-byte swizzle row
 constexpr uint32_t kABytes = kTM * kTK * 2;   // 16 KB
 
-struct DenseParams {
+// One problem of the batch (a single SpMM is a batch of one).
+struct DenseProb {
   const int32_t* tile_order;  // dense copy c holds rows tile_order[c]*128 ...
   float* C;
   int64_t ldc, M, N;
+  int64_t unit0;     // first unit of this problem in the batch's unit space
   int n_copy;        // 128-row tiles (dense copies) in the work
   int n_ntiles;      // TN-wide column tiles
   int slabs;         // K slabs of 64 per tile
-  int64_t units;     // n_copy * n_ntiles * slabs
-  int stages, accumulate, vec_ok;
+  int accumulate, vec_ok;
+};
+
+// The whole batch travels in the kernel parameters (no device allocation):
+// per problem its A and B tensor maps and its scalars.
+template <int NP>
+struct DenseTable {
+  CUtensorMap tmA[NP];
+  CUtensorMap tmB[NP];
+  DenseProb p[NP];
+  int count;
+  int64_t units;
+  int stages;
   int* status;
 };
 
@@ -49,16 +63,24 @@ __device__ __forceinline__ int64_t unit_begin(int64_t U, int64_t b, int64_t G) {
   return U * b / G;
 }
 
-template <int TN>
+// Advance the problem index q (monotone in u) so that u belongs to problem q.
+template <int NP>
+__device__ __forceinline__ void advance_problem(const DenseTable<NP>& T, int64_t u, int& q) {
+  while (q + 1 < T.count && u >= T.p[q + 1].unit0) ++q;
+}
+
+// MH = 128-row halves per CTA tile (1: 128 x TN, 2: 256 x TN sharing each B
+// stage between two MMAs, which halves B's shared-memory bytes per flop).
+template <int TN, int NP, int MH>
 __global__ void __launch_bounds__(192, 1)
-    dense_panel_kernel(const DenseParams p, const __grid_constant__ CUtensorMap tmA,
-                       const __grid_constant__ CUtensorMap tmB) {
+    dense_panel_kernel(const __grid_constant__ DenseTable<NP> T) {
   constexpr uint32_t kBBytes = (uint32_t)TN * kTK * 2;
-  constexpr uint32_t kStageBytes = kABytes + kBBytes;
+  constexpr uint32_t kStageBytes = MH * kABytes + kBBytes;
+  constexpr int NBUF = (MH * TN * 2 <= 512) ? 2 : 1;   // TMEM accumulator sets
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int S = p.stages;
+  const int S = T.stages;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * kStageBytes);
   uint64_t* empty = full + S;
   uint64_t* acc_full = empty + S;    // [2] MMA -> epilogue: accumulator ready
@@ -66,10 +88,9 @@ __global__ void __launch_bounds__(192, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u0 = unit_begin(p.units, blockIdx.x, gridDim.x);
-  const int64_t u1 = unit_begin(p.units, blockIdx.x + 1, gridDim.x);
+  const int64_t u0 = unit_begin(T.units, blockIdx.x, gridDim.x);
+  const int64_t u1 = unit_begin(T.units, blockIdx.x + 1, gridDim.x);
   if (u0 >= u1) return;
-  const int64_t per_tile = p.slabs;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -83,7 +104,7 @@ __global__ void __launch_bounds__(192, 1)
     fence_barrier_init();
   }
   if (warp == 1) {
-    tc::tmem_alloc(tmem_slot, 2 * TN);
+    tc::tmem_alloc(tmem_slot, NBUF * MH * TN);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -94,33 +115,38 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) {
     // ---------------- TMA producer -----------------------------------------
     if (lane == 0) {
-      prefetch_tensormap(&tmA);
-      prefetch_tensormap(&tmB);
       int64_t i = 0;
+      int q = 0;
       bool ok = true;
       for (int64_t u = u0; u < u1; ++u, ++i) {
+        advance_problem(T, u, q);
+        const DenseProb& P = T.p[q];
         const int st = (int)(i % S);
         const uint32_t ph = (uint32_t)(i / S) & 1u;
-        if (i >= S && !mbar_wait_bounded(&empty[st], ph ^ 1u, p.status)) {
+        if (i >= S && !mbar_wait_bounded(&empty[st], ph ^ 1u, T.status)) {
           ok = false;
           break;
         }
-        const int64_t tile = u / per_tile;
-        const int slab = (int)(u % per_tile);
-        const int copy = (int)(tile % p.n_copy);   // row tiles fastest: CTAs that
-        const int nt = (int)(tile / p.n_copy);     // run together share B in L2
+        const int64_t lu = u - P.unit0;
+        const int64_t tile = lu / P.slabs;
+        const int slab = (int)(lu % P.slabs);
+        const int mtiles = (P.n_copy + MH - 1) / MH;
+        const int mt = (int)(tile % mtiles);       // row tiles fastest: CTAs that
+        const int nt = (int)(tile / mtiles);       // run together share B in L2
         uint8_t* a_dst = smem + (size_t)st * kStageBytes;
-        uint8_t* b_dst = a_dst + kABytes;
+        uint8_t* b_dst = a_dst + MH * kABytes;
         const int k0 = slab * kTK;
         mbar_arrive_expect_tx(&full[st], kStageBytes);
-        tma_load_2d(a_dst, &tmA, k0, copy * kTM, &full[st]);
+#pragma unroll
+        for (int hh = 0; hh < MH; ++hh)   // rows past the last copy are zero-filled
+          tma_load_2d(a_dst + hh * kABytes, &T.tmA[q], k0, (mt * MH + hh) * kTM, &full[st]);
 #pragma unroll
         for (int j = 0; j < TN / 64; ++j)
-          tma_load_2d(b_dst + j * (kTK * 128), &tmB, nt * TN + 64 * j, k0, &full[st]);
+          tma_load_2d(b_dst + j * (kTK * 128), &T.tmB[q], nt * TN + 64 * j, k0, &full[st]);
       }
       if (!ok) {
         for (int64_t j = (i > S ? i - S : 0); j < i; ++j)
-          mbar_wait_bounded(&full[j % S], (uint32_t)(j / S) & 1u, p.status);
+          mbar_wait_bounded(&full[j % S], (uint32_t)(j / S) & 1u, T.status);
       }
     }
   } else if (warp == 1) {
@@ -129,111 +155,128 @@ __global__ void __launch_bounds__(192, 1)
       constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, TN, false, true);
       int64_t i = 0;
       int seg = -1;
+      int q = 0;
       bool ok = true;
       for (int64_t u = u0; u < u1 && ok; ++u, ++i) {
-        const int slab = (int)(u % per_tile);
+        advance_problem(T, u, q);
+        const DenseProb& P = T.p[q];
+        const int slab = (int)((u - P.unit0) % P.slabs);
         const bool first = (u == u0) || slab == 0;
-        const bool last = (u + 1 == u1) || slab + 1 == per_tile;
+        const bool last = (u + 1 == u1) || slab + 1 == P.slabs;
         if (first) {
           ++seg;
-          const int b = seg & 1;
-          // the epilogue must have drained this accumulator (segment seg - 2)
-          if (seg >= 2 &&
-              !mbar_wait_bounded(&acc_empty[b], (uint32_t)((seg >> 1) - 1) & 1u, p.status)) {
+          const int b = seg % NBUF;
+          // the epilogue must have drained this accumulator (segment seg - NBUF)
+          if (seg >= NBUF &&
+              !mbar_wait_bounded(&acc_empty[b], (uint32_t)((seg / NBUF) - 1) & 1u, T.status)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
         }
-        const uint32_t d_tmem = tmem + (uint32_t)((seg & 1) * TN);
+        const uint32_t d_tmem = tmem + (uint32_t)((seg % NBUF) * MH * TN);
         const int st = (int)(i % S);
         const uint32_t ph = (uint32_t)(i / S) & 1u;
-        if (!mbar_wait_bounded(&full[st], ph, p.status)) {
+        if (!mbar_wait_bounded(&full[st], ph, T.status)) {
           ok = false;
           break;
         }
         tc::fence_after_sync();
         const uint32_t a_base = smem_u32(smem + (size_t)st * kStageBytes);
-        const uint32_t b_base = a_base + kABytes;
+        const uint32_t b_base = a_base + MH * kABytes;
 #pragma unroll
         for (int kk = 0; kk < kTK / 16; ++kk) {
-          // A: K-major, 128-byte swizzle, 8-row groups 1024 B apart; a K step
-          // of 16 BF16 is 32 bytes inside the swizzle row.
-          const uint64_t ad = tc::smem_desc(a_base + kk * 32, 16, 1024, 2);
           // B: N-major (row k of B = 128 bytes of 64 N values), 128-byte
           // swizzle; 64-wide N chunks are 64 rows x 128 B = 8 KB apart (LBO),
           // 8-row K groups 1024 B apart (SBO); a K step of 16 rows = 2 KB.
           const uint64_t bd = tc::smem_desc(b_base + kk * 16 * 128, kTK * 128, 1024, 2);
-          tc::mma_bf16(d_tmem, ad, bd, idesc, (!first || kk > 0) ? 1u : 0u);
+#pragma unroll
+          for (int hh = 0; hh < MH; ++hh) {
+            // A: K-major, 128-byte swizzle, 8-row groups 1024 B apart; a K
+            // step of 16 BF16 is 32 bytes inside the swizzle row.
+            const uint64_t ad = tc::smem_desc(a_base + hh * kABytes + kk * 32, 16, 1024, 2);
+            tc::mma_bf16(d_tmem + hh * TN, ad, bd, idesc, (!first || kk > 0) ? 1u : 0u);
+          }
         }
-        tc::mma_commit(&empty[st]);                  // stage free once these MMAs finish
-        if (last) tc::mma_commit(&acc_full[seg & 1]);  // accumulator complete
+        tc::mma_commit(&empty[st]);                    // stage free once these MMAs finish
+        if (last) tc::mma_commit(&acc_full[seg % NBUF]);  // accumulator complete
       }
       if (!ok) {
         // make the epilogue's waits end: release every accumulator it expects
-        for (int b = 0; b < 2; ++b) tc::mma_commit(&acc_full[b]);
+        for (int b = 0; b < NBUF; ++b) tc::mma_commit(&acc_full[b]);
       }
     }
   } else {
     // ---------------- epilogue: TMEM -> registers -> C -----------------------
     const int quarter = warp & 3;
     int seg = -1;
+    int q = 0;
     for (int64_t u = u0; u < u1; ++u) {
-      const int slab = (int)(u % per_tile);
+      advance_problem(T, u, q);
+      const DenseProb& P = T.p[q];
+      const int64_t lu = u - P.unit0;
+      const int slab = (int)(lu % P.slabs);
       const bool first = (u == u0) || slab == 0;
       if (!first) continue;
       ++seg;
       // segment [u, ue): slabs of one tile
-      int64_t ue = u - slab + per_tile;
+      int64_t ue = u - slab + P.slabs;
       if (ue > u1) ue = u1;
-      const bool whole = (slab == 0) && (ue - u == per_tile);
-      const int64_t tile = u / per_tile;
-      const int copy = (int)(tile % p.n_copy);
-      const int nt = (int)(tile / p.n_copy);
-      const int b = seg & 1;
-      const bool ok = mbar_wait_bounded(&acc_full[b], (uint32_t)(seg >> 1) & 1u, p.status);
+      const bool whole = (slab == 0) && (ue - u == P.slabs);
+      const int64_t tile = lu / P.slabs;
+      const int mtiles = (P.n_copy + MH - 1) / MH;
+      const int mt = (int)(tile % mtiles);
+      const int nt = (int)(tile / mtiles);
+      const int b = seg % NBUF;
+      const bool ok = mbar_wait_bounded(&acc_full[b], (uint32_t)(seg / NBUF) & 1u, T.status);
       tc::fence_after_sync();
-      const int64_t row = (int64_t)__ldg(&p.tile_order[copy]) * kTM + quarter * 32 + lane;
       const int64_t n0 = (int64_t)nt * TN;
 #pragma unroll 1
-      for (int c = 0; c < TN / 32; ++c) {
-        uint32_t r[32];
-        tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * TN + c * 32),
-                               r);
-        tc::tmem_ld_wait();
-        const int64_t col0 = n0 + c * 32;
-        if (!ok || row >= p.M || col0 >= p.N) continue;
-        float* dst = p.C + row * p.ldc + col0;
-        const bool vec = p.vec_ok && col0 + 32 <= p.N;
-        if (!whole) {
-          // a K range of a split tile: add into C (zeroed beforehand unless
-          // the call accumulates)
-          if (vec) {
+      for (int hh = 0; hh < MH; ++hh) {
+        const int copy = mt * MH + hh;
+        if (copy >= P.n_copy) break;   // warp-uniform
+        const int64_t row = (int64_t)__ldg(&P.tile_order[copy]) * kTM + quarter * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < TN / 32; ++c) {
+          uint32_t r[32];
+          tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(quarter * 32) << 16) +
+                                     (uint32_t)(b * MH * TN + hh * TN + c * 32),
+                                 r);
+          tc::tmem_ld_wait();
+          const int64_t col0 = n0 + c * 32;
+          if (!ok || row >= P.M || col0 >= P.N) continue;
+          float* dst = P.C + row * P.ldc + col0;
+          const bool vec = P.vec_ok && col0 + 32 <= P.N;
+          if (!whole) {
+            // a K range of a split tile: add into C (zeroed beforehand unless
+            // the call accumulates)
+            if (vec) {
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              atomicAdd(reinterpret_cast<float4*>(dst + j),
-                        make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                    __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])));
+              for (int j = 0; j < 32; j += 4)
+                atomicAdd(reinterpret_cast<float4*>(dst + j),
+                          make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                      __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (col0 + j < P.N) atomicAdd(dst + j, __uint_as_float(r[j]));
+            }
+          } else if (vec) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                     __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+              if (P.accumulate) {
+                const float4 o = *reinterpret_cast<const float4*>(dst + j);
+                v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+              }
+              *reinterpret_cast<float4*>(dst + j) = v;
+            }
           } else {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (col0 + j < p.N) atomicAdd(dst + j, __uint_as_float(r[j]));
+              if (col0 + j < P.N) dst[j] = __uint_as_float(r[j]) + (P.accumulate ? dst[j] : 0.0f);
           }
-        } else if (vec) {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-            if (p.accumulate) {
-              const float4 o = *reinterpret_cast<const float4*>(dst + j);
-              v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
-            }
-            *reinterpret_cast<float4*>(dst + j) = v;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (col0 + j < p.N) dst[j] = __uint_as_float(r[j]) + (p.accumulate ? dst[j] : 0.0f);
         }
       }
       // accumulator drained: hand it back to the MMA issuer
@@ -245,94 +288,175 @@ __global__ void __launch_bounds__(192, 1)
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 1) tc::tmem_dealloc(tmem, 2 * TN);
+  if (warp == 1) tc::tmem_dealloc(tmem, NBUF * MH * TN);
 }
 
-template <int TN>
+template <int TN, int MH>
 size_t dense_smem_bytes(int stages) {
-  return 1024 + (size_t)stages * (kABytes + (size_t)TN * kTK * 2) + 256;
+  return 1024 + (size_t)stages * (MH * kABytes + (size_t)TN * kTK * 2) + 256;
 }
 
-}  // namespace
-
-// True when the stream-K split leaves some tile with more than one K range
-// (those tiles are accumulated with atomics into a zeroed C).
-int64_t dense_grid(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas) {
-  const int64_t slabs = (K + kTK - 1) / kTK;
-  const int64_t units = n_tiles * ((N + TN - 1) / TN) * slabs;
-  return std::max<int64_t>(1, std::min<int64_t>(ctas, units));
+template <int TN, int MH>
+constexpr int dense_stages() {
+  return (200 * 1024) / (MH * kABytes + TN * kTK * 2) > 6 ? 6
+                                                         : (200 * 1024) / (MH * kABytes + TN * kTK * 2);
 }
 
-bool dense_needs_zero(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas) {
-  const int64_t slabs = (K + kTK - 1) / kTK;
-  const int64_t units = n_tiles * ((N + TN - 1) / TN) * slabs;
-  const int64_t G = dense_grid(n_tiles, N, K, TN, ctas);
-  for (int64_t b = 0; b <= G; ++b) {
-    const int64_t u = units * b / G;
-    if (u % slabs != 0 && u != units) return true;
-  }
-  return false;
-}
+int64_t slabs_of(int64_t K) { return (K + kTK - 1) / kTK; }
 
-rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t Kpad,
-                               const int32_t* tile_order_dev, int64_t n_tiles, int64_t K,
-                               const void* B, int64_t N, int64_t ldb, float* C, int64_t ldc,
-                               int64_t M, int accumulate, int TN, int ctas, bool c_zeroed,
-                               cudaStream_t st) {
-  if (n_tiles <= 0 || N <= 0) return ROSKO_OK;
-  if (ctas <= 0) ctas = num_sms();
-  if (TN != 128 && TN != 256) return ROSKO_ERR_INVALID_ARG;
-  const int stages = (TN == 256) ? 4 : 6;
-  const size_t smem = TN == 256 ? dense_smem_bytes<256>(stages) : dense_smem_bytes<128>(stages);
-  static size_t set128 = 0, set256 = 0;
-  size_t& set = TN == 256 ? set256 : set128;
-  auto fn = TN == 256 ? dense_panel_kernel<256> : dense_panel_kernel<128>;
+template <int TN, int NP, int MH>
+rosko_status launch_table(DenseTable<NP>& T, int64_t grid, cudaStream_t st) {
+  const size_t smem = dense_smem_bytes<TN, MH>(T.stages);
+  static size_t set = 0;
+  auto fn = dense_panel_kernel<TN, NP, MH>;
   if (smem > set) {
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
       return ROSKO_ERR_CUDA;
     set = smem;
   }
-  CUtensorMap mapA, mapB;
+  fn<<<(unsigned)grid, 192, smem, st>>>(T);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+}
+
+rosko_status encode_dense_maps(const DenseJob& j, CUtensorMap* mA, CUtensorMap* mB) {
   {
-    const cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)dense_rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)Kpad * 2};
+    const cuuint64_t dims[2] = {(cuuint64_t)j.Kpad, (cuuint64_t)j.dense_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)j.Kpad * 2};
     const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
     const cuuint32_t es[2] = {1, 1};
-    if (encode_tiled(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(dense_A), dims,
+    if (encode_tiled(mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(j.dense_A), dims,
                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return ROSKO_ERR_INVALID_ARG;
   }
   {
-    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)K};
-    const cuuint64_t strides[1] = {(cuuint64_t)ldb * 2};
+    const cuuint64_t dims[2] = {(cuuint64_t)j.N, (cuuint64_t)j.K};
+    const cuuint64_t strides[1] = {(cuuint64_t)j.ldb * 2};
     const cuuint32_t box[2] = {64, (cuuint32_t)kTK};
     const cuuint32_t es[2] = {1, 1};
-    if (encode_tiled(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(B), dims,
+    if (encode_tiled(mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(j.B), dims,
                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return ROSKO_ERR_INVALID_ARG;
   }
-  DenseParams p{};
-  p.tile_order = tile_order_dev;
-  p.C = C;
-  p.ldc = ldc;
-  p.M = M;
-  p.N = N;
-  p.n_copy = (int)n_tiles;
-  p.n_ntiles = (int)((N + TN - 1) / TN);
-  p.slabs = (int)((K + kTK - 1) / kTK);
-  p.units = (int64_t)p.n_copy * p.n_ntiles * p.slabs;
-  p.stages = stages;
-  p.accumulate = accumulate;
-  p.vec_ok = ((reinterpret_cast<uintptr_t>(C) % 16) == 0) && ((ldc * 4) % 16 == 0);
-  p.status = device_status_word();
-  if (!p.status) return ROSKO_ERR_CUDA;
-  const int64_t G = dense_grid(n_tiles, N, K, TN, ctas);
-  if (!accumulate && !c_zeroed && dense_needs_zero(n_tiles, N, K, TN, ctas)) {
+  return ROSKO_OK;
+}
+
+template <int TN, int NP, int MH>
+rosko_status run_jobs(const DenseJob* jobs, int count, int ctas, cudaStream_t st) {
+  static_assert(sizeof(DenseTable<NP>) <= 30 * 1024, "kernel parameter table too large");
+  DenseTable<NP> T;
+  std::memset(static_cast<void*>(&T), 0, sizeof(T));
+  int64_t units = 0;
+  int n = 0;
+  for (int i = 0; i < count; ++i) {
+    const DenseJob& j = jobs[i];
+    if (j.n_tiles <= 0 || j.N <= 0) continue;
+    rosko_status s = encode_dense_maps(j, &T.tmA[n], &T.tmB[n]);
+    if (s != ROSKO_OK) return s;
+    DenseProb& P = T.p[n];
+    P.tile_order = j.tile_order_dev;
+    P.C = j.C;
+    P.ldc = j.ldc;
+    P.M = j.M;
+    P.N = j.N;
+    P.unit0 = units;
+    P.n_copy = (int)j.n_tiles;
+    P.n_ntiles = (int)((j.N + TN - 1) / TN);
+    P.slabs = (int)slabs_of(j.K);
+    P.accumulate = j.accumulate;
+    P.vec_ok = ((reinterpret_cast<uintptr_t>(j.C) % 16) == 0) && ((j.ldc * 4) % 16 == 0);
+    units += (int64_t)((P.n_copy + MH - 1) / MH) * P.n_ntiles * P.slabs;
+    ++n;
+  }
+  if (n == 0) return ROSKO_OK;
+  T.count = n;
+  T.units = units;
+  T.stages = dense_stages<TN, MH>();
+  T.status = device_status_word();
+  if (!T.status) return ROSKO_ERR_CUDA;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ctas, units));
+  return launch_table<TN, NP, MH>(T, grid, st);
+}
+
+}  // namespace
+
+static int64_t job_units(int64_t n_tiles, int64_t N, int64_t K, int TN, int MH) {
+  return ((n_tiles + MH - 1) / MH) * ((N + TN - 1) / TN) * slabs_of(K);
+}
+
+int64_t dense_grid(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas, int MH) {
+  return std::max<int64_t>(1, std::min<int64_t>(ctas, job_units(n_tiles, N, K, TN, MH)));
+}
+
+// True when the stream-K split of `units` over `ctas` CTAs cuts some tile of
+// `slabs` units (those tiles are accumulated with atomics into a zeroed C).
+static bool split_cuts_tile(int64_t units_before, int64_t units, int64_t total, int64_t slabs,
+                            int64_t G) {
+  for (int64_t b = 0; b <= G; ++b) {
+    const int64_t u = total * b / G;
+    if (u <= units_before || u >= units_before + units) continue;
+    if ((u - units_before) % slabs != 0) return true;
+  }
+  return false;
+}
+
+bool dense_needs_zero(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas, int MH) {
+  const int64_t units = job_units(n_tiles, N, K, TN, MH);
+  const int64_t G = dense_grid(n_tiles, N, K, TN, ctas, MH);
+  return split_cuts_tile(0, units, units, slabs_of(K), G);
+}
+
+// For a batch: which jobs have a tile cut between CTAs (job order as given).
+void dense_batch_needs_zero(const DenseJob* jobs, int count, int TN, int ctas, int MH,
+                            bool* out) {
+  int64_t total = 0;
+  for (int i = 0; i < count; ++i)
+    if (jobs[i].n_tiles > 0 && jobs[i].N > 0)
+      total += job_units(jobs[i].n_tiles, jobs[i].N, jobs[i].K, TN, MH);
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(ctas, total));
+  int64_t before = 0;
+  for (int i = 0; i < count; ++i) {
+    out[i] = false;
+    if (jobs[i].n_tiles <= 0 || jobs[i].N <= 0) continue;
+    const int64_t units = job_units(jobs[i].n_tiles, jobs[i].N, jobs[i].K, TN, MH);
+    out[i] = split_cuts_tile(before, units, total, slabs_of(jobs[i].K), G);
+    before += units;
+  }
+}
+
+template <int NP>
+static rosko_status dispatch_jobs(const DenseJob* jobs, int count, int TN, int MH, int ctas,
+                                  cudaStream_t st) {
+  if (TN == 256 && MH == 2) return run_jobs<256, NP, 2>(jobs, count, ctas, st);
+  if (TN == 256) return run_jobs<256, NP, 1>(jobs, count, ctas, st);
+  if (MH == 2) return run_jobs<128, NP, 2>(jobs, count, ctas, st);
+  return run_jobs<128, NP, 1>(jobs, count, ctas, st);
+}
+
+rosko_status dense_batch_launch(const DenseJob* jobs, int count, int TN, int ctas, int MH,
+                                cudaStream_t st) {
+  if (count <= 0) return ROSKO_OK;
+  if ((TN != 128 && TN != 256) || (MH != 1 && MH != 2)) return ROSKO_ERR_INVALID_ARG;
+  if (ctas <= 0) ctas = num_sms();
+  if (count == 1) return dispatch_jobs<1>(jobs, 1, TN, MH, ctas, st);
+  if (count <= 64) return dispatch_jobs<64>(jobs, count, TN, MH, ctas, st);
+  return ROSKO_ERR_INVALID_ARG;
+}
+
+rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t Kpad,
+                               const int32_t* tile_order_dev, int64_t n_tiles, int64_t K,
+                               const void* B, int64_t N, int64_t ldb, float* C, int64_t ldc,
+                               int64_t M, int accumulate, int TN, int ctas, int MH,
+                               bool c_zeroed, cudaStream_t st) {
+  if (n_tiles <= 0 || N <= 0) return ROSKO_OK;
+  if (TN != 128 && TN != 256) return ROSKO_ERR_INVALID_ARG;
+  if (ctas <= 0) ctas = num_sms();
+  if (!accumulate && !c_zeroed && dense_needs_zero(n_tiles, N, K, TN, ctas, MH)) {
     // zero the C rows of every dense tile (tiles are disjoint row blocks)
     std::vector<int32_t> order((size_t)n_tiles);
     if (cudaMemcpyAsync(order.data(), tile_order_dev, order.size() * 4, cudaMemcpyDeviceToHost,
@@ -348,9 +472,21 @@ rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t 
         return ROSKO_ERR_CUDA;
     }
   }
-  fn<<<(unsigned)G, 192, smem, st>>>(p, mapA, mapB);
-  count_launches(1);
-  return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+  DenseJob j;
+  j.dense_A = dense_A;
+  j.dense_rows = dense_rows;
+  j.Kpad = Kpad;
+  j.tile_order_dev = tile_order_dev;
+  j.n_tiles = n_tiles;
+  j.K = K;
+  j.B = B;
+  j.N = N;
+  j.ldb = ldb;
+  j.C = C;
+  j.ldc = ldc;
+  j.M = M;
+  j.accumulate = accumulate;
+  return dense_batch_launch(&j, 1, TN, ctas, MH, st);
 }
 
 }  // namespace rosko

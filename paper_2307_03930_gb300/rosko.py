@@ -39,7 +39,7 @@ class rosko_tile(ctypes.Structure):
                 ("m_c", ctypes.c_int32), ("split_k", ctypes.c_int32),
                 ("dense_split_pm", ctypes.c_int32), ("dense_n_r", ctypes.c_int32),
                 ("dense_split_k", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("mode", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("dense_m_c", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
                                 ctypes.c_float, ctypes.c_float, vp]),
         "rosko_selector_set": (ci, [ctypes.POINTER(ctypes.c_float), i64] +
                                [ctypes.POINTER(ctypes.c_double)] * 4),
+        "rosko_spmm_batched": (ci, [i32, vp, vp, vp, vp, vp, vp, ci, ci, ci, P_tile, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -340,3 +341,24 @@ def rosko_selector_set(params_host, mean, std, lo, hi) -> None:
     dp = ctypes.POINTER(ctypes.c_double)
     _check(lib().rosko_selector_set(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size,
                                     *[a.ctypes.data_as(dp) for a in arr]), "rosko_selector_set")
+
+
+def rosko_spmm_batched(As, Bs, Cs, accumulate: bool = False, tiles=None, stream=None):
+    """C_i = A_i . B_i for up to 64 problems in one dense-panel launch plus one
+    sparse launch per problem that needs it."""
+    n = len(As)
+    h = (ctypes.c_void_p * n)(*[a.handle.value for a in As])
+    b = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Bs])
+    c = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Cs])
+    N = (ctypes.c_int64 * n)(*[x.shape[1] for x in Bs])
+    ldb = (ctypes.c_int64 * n)(*[_ld(x) for x in Bs])
+    ldc = (ctypes.c_int64 * n)(*[_ld(x) for x in Cs])
+    tl = None
+    if tiles is not None:
+        tl = (rosko_tile * n)(*tiles)
+    st = lib().rosko_spmm_batched(n, h, b, N, ldb, c, ldc, TORCH_TO_CODE[Bs[0].dtype],
+                                  TORCH_TO_CODE[Cs[0].dtype], int(bool(accumulate)),
+                                  ctypes.cast(tl, ctypes.POINTER(rosko_tile)) if tl is not None else None,
+                                  ctypes.c_void_p(_stream(stream)))
+    _check(st, "rosko_spmm_batched")
+    return Cs

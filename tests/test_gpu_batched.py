@@ -1,0 +1,89 @@
+"""Batched SpMM (one persistent stream-K tensor-core launch for every
+problem's dense tiles, sparse remainders per problem) against the oracle, and
+its capture/replay in a CUDA graph.  GPU only."""
+import numpy as np
+import pytest
+import torch
+
+from tests._lib import built
+from tests.test_gpu_spmm import _ldpad
+from oracle.spmm import spmm, normalized_error
+from oracle.quant import bf16_round
+from paper_2307_03930_gb300 import inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems(seed, shapes):
+    out = []
+    for j, (M, K, N, s, pat) in enumerate(shapes):
+        A = gen.sparse_weight(M, K, s, gen.rng_for(seed, j), pat)
+        B = gen.relu_normal((K, N), gen.rng_for(seed, 100 + j))
+        out.append((A, B))
+    return out
+
+
+SHAPES = [(300, 500, 257, 0.7, "uniform"), (64, 96, 196, 0.99, "uniform"),
+          (513, 1000, 700, 0.95, "powerlaw"), (130, 77, 300, 0.999, "uniform"),
+          (256, 640, 128, 0.9, "block4x1"), (1000, 300, 450, 0.985, "powerlaw")]
+
+
+def _run_batched(rosko, probs, tiles=None, accumulate=False, C0s=None):
+    hs = [rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16) for A, _ in probs]
+    Bs = [_ldpad(torch.from_numpy(B).to(torch.bfloat16), 2) for _, B in probs]
+    Cs = [torch.zeros((A.shape[0], B.shape[1]), device="cuda") for A, B in probs]
+    if C0s is not None:
+        for C, C0 in zip(Cs, C0s):
+            C.copy_(torch.from_numpy(C0))
+    l0 = rosko.rosko_kernel_launches()
+    rosko.rosko_spmm_batched(hs, Bs, Cs, accumulate=accumulate, tiles=tiles)
+    torch.cuda.synchronize()
+    assert rosko.rosko_device_status(clear=True) == 0
+    return hs, Bs, Cs, rosko.rosko_kernel_launches() - l0
+
+
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_batched_matches_oracle(accumulate):
+    rosko = built()
+    probs = _problems(71, SHAPES)
+    C0s = [np.random.default_rng(j).standard_normal((A.shape[0], B.shape[1])).astype(np.float32)
+           for j, (A, B) in enumerate(probs)] if accumulate else None
+    hs, Bs, Cs, launches = _run_batched(rosko, probs, accumulate=accumulate, C0s=C0s)
+    for j, ((A, B), C) in enumerate(zip(probs, Cs)):
+        ref, D = spmm(bf16_round(A), bf16_round(B), C0=C0s[j] if accumulate else None)
+        if accumulate:
+            D = D + np.abs(C0s[j])
+        assert normalized_error(C.cpu().numpy(), ref, D) <= 1e-5, j
+    # one dense launch for all problems + at most one sparse launch per problem
+    assert launches <= 1 + len(probs)
+
+
+@pytest.mark.parametrize("MC", [128, 256])
+def test_batched_forced_dense_for_all(MC):
+    rosko = built()
+    probs = _problems(72, SHAPES)
+    tiles = [rosko.make_tile(dense_split_pm=1, dense_m_c=MC) for _ in probs]
+    hs, Bs, Cs, launches = _run_batched(rosko, probs, tiles=tiles)
+    for (A, B), C in zip(probs, Cs):
+        ref, D = spmm(bf16_round(A), bf16_round(B))
+        assert normalized_error(C.cpu().numpy(), ref, D) <= 1e-5
+    # every tile has density >= 1 per mille except the 99.9% problem's
+    assert launches <= 2
+
+
+def test_batched_graph_capture_and_replay():
+    rosko = built()
+    probs = _problems(73, SHAPES[:4])
+    hs, Bs, Cs, _ = _run_batched(rosko, probs)       # first call outside capture
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rosko.rosko_spmm_batched(hs, Bs, Cs)
+    # new activations in place, replay
+    new_B = [gen.relu_normal(B.shape, gen.rng_for(74, j)) for j, (_, B) in enumerate(probs)]
+    for Bd, Bn in zip(Bs, new_B):
+        Bd.copy_(torch.from_numpy(Bn).to(torch.bfloat16))
+    g.replay()
+    torch.cuda.synchronize()
+    for (A, _), Bn, C in zip(probs, new_B, Cs):
+        ref, D = spmm(bf16_round(A), bf16_round(Bn))
+        assert normalized_error(C.cpu().numpy(), ref, D) <= 1e-5

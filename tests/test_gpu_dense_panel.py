@@ -38,26 +38,29 @@ def _run(rosko, A, B, tile, rows=None, accumulate=False, C0=None, dense_min_pm=0
 @pytest.mark.parametrize("M,K,N", [(128, 64, 128), (130, 77, 257), (256, 1000, 300),
                                    (1, 8, 1), (300, 129, 64), (384, 2048, 520)])
 @pytest.mark.parametrize("TN,ctas", [(128, 0), (256, 0), (256, 7), (128, 1), (256, 3)])
-def test_all_dense(M, K, N, TN, ctas):
+@pytest.mark.parametrize("MC", [128, 256])
+def test_all_dense(M, K, N, TN, ctas, MC):
     # stream-K over `ctas` CTAs (0: one per SM): tiles whose K range is cut
-    # between CTAs are added with atomics, whole tiles are stored
+    # between CTAs are added with atomics, whole tiles are stored; MC = 256
+    # pairs two 128-row tiles per CTA tile (an odd tile count leaves the
+    # second half of the last pair empty)
     rosko = built()
     A = gen.sparse_weight(M, K, 0.5, gen.rng_for(7, M, K), "uniform")
     B = gen.normal((K, N), gen.rng_for(8, K, N))
-    t = rosko.make_tile(dense_split_pm=1, dense_n_r=TN, dense_split_k=ctas)
+    t = rosko.make_tile(dense_split_pm=1, dense_n_r=TN, dense_split_k=ctas, dense_m_c=MC)
     err, launches = _run(rosko, A, B, t)
     assert err <= 1e-5, err
     assert launches == 1          # only the tensor-core kernel ran
 
 
-def test_mixed_split_powerlaw():
+@pytest.mark.parametrize("MC", [128, 256])
+def test_mixed_split_powerlaw(MC):
     # power-law rows give tiles of very different density: some run dense,
     # the others on the sparse kernel, in one call
     rosko = built()
     A = gen.sparse_weight(1000, 700, 0.97, gen.rng_for(9), "powerlaw")
     B = gen.relu_normal((700, 333), gen.rng_for(10))
-    h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16)
-    t = rosko.make_tile(dense_split_pm=30)
+    t = rosko.make_tile(dense_split_pm=30, dense_m_c=MC)
     err, launches = _run(rosko, A, B, t)
     assert err <= 1e-5, err
     dens = [(A[i:i + 128] != 0).mean() for i in range(0, 1000, 128)]
@@ -67,14 +70,25 @@ def test_mixed_split_powerlaw():
 
 
 @pytest.mark.parametrize("ctas", [1, 5, 0])
-def test_dense_accumulate(ctas):
+@pytest.mark.parametrize("MC", [128, 256])
+def test_dense_accumulate(ctas, MC):
     rosko = built()
     A = gen.sparse_weight(200, 512, 0.8, gen.rng_for(11), "uniform")
     B = gen.normal((512, 200), gen.rng_for(12))
     C0 = np.random.default_rng(3).standard_normal((200, 200)).astype(np.float32)
-    t = rosko.make_tile(dense_split_pm=1, dense_split_k=ctas)
+    t = rosko.make_tile(dense_split_pm=1, dense_split_k=ctas, dense_m_c=MC)
     err, _ = _run(rosko, A, B, t, accumulate=True, C0=C0)
     assert err <= 1e-5, err
+
+
+def test_bad_dense_m_c_rejected():
+    rosko = built()
+    A = gen.sparse_weight(256, 64, 0.5, gen.rng_for(15), "uniform")
+    h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16)
+    B = _ldpad(torch.zeros((64, 64), dtype=torch.bfloat16), 2)
+    C = torch.zeros((256, 64), device="cuda")
+    with pytest.raises(RuntimeError):
+        rosko.rosko_spmm(h, B, C, tile=rosko.make_tile(dense_split_pm=1, dense_m_c=192))
 
 
 def test_no_copy_means_sparse_only():

@@ -91,10 +91,13 @@ def test_adam_matches_oracle():
     m = (rng.standard_normal(n) * 0.1).astype(np.float32)
     v = (rng.random(n) * 0.01).astype(np.float32)
     tp, tg, tm, tv = [torch.from_numpy(x.copy()).cuda() for x in (p, g, m, v)]
-    rosko.rosko_mlp_adam(tp, tg, tm, tv, step=7, lr=3e-3)
+    # hyper-parameters exactly representable in FP32, so that both sides use
+    # the same beta values (1 - beta is then exact in FP32 as well)
+    b1, b2, lr = float(np.float32(0.9)), float(np.float32(0.999)), float(np.float32(3e-3))
+    rosko.rosko_mlp_adam(tp, tg, tm, tv, step=7, lr=lr, beta1=b1, beta2=b2)
     (rp,), (rm,), (rv,) = omlp.adam_step([p.astype(np.float64)], [g.astype(np.float64)],
                                          [m.astype(np.float64)], [v.astype(np.float64)], t=7,
-                                         lr=3e-3)
+                                         lr=lr, beta1=b1, beta2=b2)
     assert np.allclose(tp.cpu().numpy(), rp, rtol=1e-5, atol=1e-6)
     assert np.allclose(tm.cpu().numpy(), rm, rtol=1e-5, atol=1e-7)
     assert np.allclose(tv.cpu().numpy(), rv, rtol=1e-5, atol=1e-9)

@@ -276,6 +276,30 @@ rosko_status rosko_time_tile(rosko_packed_t A, const void* B_dev, rosko_dtype b_
 rosko_status rosko_features(rosko_packed_t A, int64_t N, double* features16, rosko_stream_t stream);
 
 /*
+ * rosko_features_static - the same 16 features, computed in FP32 on the
+ * device, for callers that must not allocate device memory (fixed memory
+ * pools, latency-critical serving).  The paper has no counterpart: it is a
+ * variant of rosko_features whose scratch is a static device array of this
+ * library instead of a per-call cudaMalloc.
+ *
+ * features16_dev  16 floats of device memory (4-byte aligned), written in
+ *         stream order; the caller owns it.
+ * Allocates no device memory and does not synchronise.  Limits and races:
+ *   - A->M must be <= 1048576 (the static array's rows), else
+ *     ROSKO_ERR_INVALID_ARG before anything is enqueued;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current): make it once before
+ *     any stream capture;
+ *   - every call shares the one array per device and clears it first, so
+ *     calls that can overlap on the GPU (different streams, or several host
+ *     threads) race and may return wrong features: serialise them.
+ * Errors: ROSKO_ERR_BAD_HANDLE, ROSKO_ERR_INVALID_ARG (NULL or misaligned
+ * output, N < 1, M too large), ROSKO_ERR_CUDA (a launch or memset failed).
+ */
+rosko_status rosko_features_static(rosko_packed_t A, int64_t N, float* features16_dev,
+                                   rosko_stream_t stream);
+
+/*
  * The selector network: n_in -> 64 -> 64 -> 64 -> n_out, ReLU on the hidden
  * layers, FP32.  Parameters are one flat device array, per layer the weight
  * matrix [out][in] row-major followed by the bias [out].

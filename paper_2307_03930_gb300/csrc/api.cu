@@ -754,6 +754,14 @@ rosko_status rosko_features(rosko_packed_t A, int64_t N, double* features16,
   return features_impl(A, N, features16, static_cast<cudaStream_t>(stream));
 }
 
+rosko_status rosko_features_static(rosko_packed_t A, int64_t N, float* features16_dev,
+                                   rosko_stream_t stream) {
+  if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
+  if (!features16_dev || N < 1 || reinterpret_cast<uintptr_t>(features16_dev) % 4 != 0)
+    return ROSKO_ERR_INVALID_ARG;
+  return features_static_impl(A, N, features16_dev, static_cast<cudaStream_t>(stream));
+}
+
 int64_t rosko_mlp_param_count(int32_t n_in, int32_t n_out) {
   if (n_in < 1 || n_out < 1) return 0;
   return mlp_param_count(n_in, n_out);

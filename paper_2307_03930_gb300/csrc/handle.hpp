@@ -183,6 +183,10 @@ rosko_status autotune_impl(rosko_packed_s* h, const void* B, rosko_dtype b_dt, i
 // selector.cu
 rosko_status select_learned(rosko_packed_s* h, int64_t N, rosko_tile* out, cudaStream_t st);
 rosko_status features_impl(rosko_packed_s* h, int64_t N, double* f, cudaStream_t st);
+// Allocation-free variant: FP32 features written to device memory, scratch
+// in a static device array (M <= 1 << 20).
+rosko_status features_static_impl(rosko_packed_s* h, int64_t N, float* features_dev,
+                                  cudaStream_t st);
 int64_t mlp_param_count(int n_in, int n_out);
 int64_t mlp_workspace_floats(int64_t batch, int n_out);
 rosko_status mlp_forward(const float* params, const float* X, int64_t batch, int n_in, int n_out,

@@ -311,6 +311,95 @@ rosko_status features_impl(rosko_packed_s* h, int64_t N, double* f, cudaStream_t
   return ROSKO_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free feature statistics (no counterpart in the paper).
+//
+// Some callers must not allocate device memory: processes whose device
+// memory is handed out by a fixed pool, and latency-critical serving paths
+// where cudaMalloc/cudaFree may synchronise the device.  For them the
+// feature-statistics kernels above also run on scratch that lives in a
+// file-scope device array: every GPU that loads this library holds it
+// (4 MiB + 256 B) until the process exits.  Every call shares it and it keeps
+// the previous call's contents, so each call clears what must start at zero;
+// calls that overlap on the GPU (two streams, two host threads) race on it.
+// The largest M served is kStaticRows; larger handles are rejected.
+constexpr int64_t kStaticRows = 1 << 20;   // largest M the static scratch serves
+static __device__ __align__(256) int32_t g_static_scratch[kStaticRows + 64];
+
+namespace {
+// Features from the integer statistics, on the device: the same definitions
+// as features_impl, evaluated in double and stored as FP32.
+__global__ void features_finish_kernel(const unsigned long long* __restrict__ s, int64_t M,
+                                       int64_t K, int64_t N, int64_t P, float* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double f[16];
+  const double Md = (double)M, Kd = (double)K, nnz = (double)s[0];
+  const double mean_row = M ? nnz / Md : 0.0;
+  f[0] = log2(Md);
+  f[1] = log2(Kd);
+  f[2] = log2((double)N);
+  f[3] = (M && K) ? nnz / (Md * Kd) : 0.0;
+  f[4] = log2(1.0 + nnz);
+  f[5] = log2(1.0 + mean_row);
+  const double var = M ? (double)s[1] / Md - mean_row * mean_row : 0.0;
+  f[6] = mean_row > 0 ? sqrt(fmax(var, 0.0)) / mean_row : 0.0;
+  f[7] = log2(1.0 + (double)s[2]) - log2(1.0 + mean_row);
+  for (int j = 0; j < 4; ++j) f[8 + j] = M ? (double)s[3 + j] / Md : 0.0;
+  const double Pd = (double)P;
+  f[12] = (P && K) ? (double)s[7] / (Pd * Kd) : 0.0;
+  const double mean_p = P ? nnz / Pd : 0.0;
+  const double var_p = P ? (double)s[8] / Pd - mean_p * mean_p : 0.0;
+  f[13] = mean_p > 0 ? sqrt(fmax(var_p, 0.0)) / mean_p : 0.0;
+  f[14] = log2(1.0 + (s[7] ? nnz / (double)s[7] : 0.0));
+  f[15] = P ? (double)s[9] / Pd : 0.0;
+  for (int j = 0; j < 16; ++j) out[j] = (float)f[j];
+}
+}  // namespace
+
+// Device address of the static scratch, looked up once per device with that
+// device current (in host code the array's name is only a stand-in).
+static int32_t* static_scratch_address() {
+  static int32_t* addr[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<int32_t*>(p);
+  }
+  return addr[dev];
+}
+
+rosko_status features_static_impl(rosko_packed_s* h, int64_t N, float* features_dev,
+                                  cudaStream_t st) {
+  const int64_t M = h->M, K = h->K, P = h->P;
+  if (M > kStaticRows) return ROSKO_ERR_INVALID_ARG;
+  int32_t* base = static_scratch_address();
+  if (!base) return ROSKO_ERR_CUDA;
+  int32_t* rowcnt = base;
+  auto* stats = reinterpret_cast<unsigned long long*>(base + kStaticRows);
+  // the previous call's counts are still there: clear rows and statistics
+  if ((M > 0 && cudaMemsetAsync(rowcnt, 0, (size_t)M * 4, st) != cudaSuccess) ||
+      cudaMemsetAsync(stats, 0, 10 * sizeof(unsigned long long), st) != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  if (P > 0 && h->nnz > 0) {
+    row_counts_kernel<<<(unsigned)P, 128, 0, st>>>(h->panel_col, h->colrec, h->nz, h->dt, h->m_r,
+                                                   rowcnt);
+    count_launches(1);
+  }
+  if (M > 0) {
+    const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>((M + 255) / 256, 1), 256);
+    feature_stats_kernel<<<nb, 256, 0, st>>>(rowcnt, M, K, h->panel_col, h->panel_nnz_dev, P,
+                                              stats);
+    count_launches(1);
+  }
+  features_finish_kernel<<<1, 32, 0, st>>>(stats, M, K, N, P, features_dev);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+}
+
 rosko_status selector_set(const float* params, int n_params, int n_out, const double* mean,
                           const double* stdv, const double* lo, const double* hi) {
   if (n_out != num_candidates() || n_params != mlp_param_count(kNumFeatures, n_out))

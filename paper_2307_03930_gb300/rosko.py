@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
         "rosko_time_tile": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, P_tile, i32,
                                  ctypes.POINTER(ctypes.c_float), vp]),
         "rosko_features": (ci, [vp, i64, ctypes.POINTER(ctypes.c_double), vp]),
+        "rosko_features_static": (ci, [vp, i64, vp, vp]),
         "rosko_mlp_param_count": (i64, [i32, i32]),
         "rosko_mlp_workspace_floats": (i64, [i64, i32]),
         "rosko_mlp_forward": (ci, [vp, vp, i64, i32, i32, vp, vp, vp]),
@@ -291,6 +292,20 @@ def rosko_features(A: PackedA, N: int, stream=None):
     _check(lib().rosko_features(A.handle, N, f, ctypes.c_void_p(_stream(stream))),
            "rosko_features")
     return np.array(f[:], dtype=np.float64)
+
+
+def rosko_features_static(A: PackedA, N: int, out=None, stream=None):
+    """FP32 features into a 16-float CUDA tensor (allocation-free library
+    path; `out` is allocated here by torch when not given)."""
+    import torch
+    if out is None:
+        out = torch.empty(16, dtype=torch.float32, device="cuda")
+    if out.dtype != torch.float32 or not out.is_cuda or out.numel() < 16 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA float32 tensor of >= 16 elements")
+    _check(lib().rosko_features_static(A.handle, N, ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(_stream(stream))),
+           "rosko_features_static")
+    return out
 
 
 def rosko_mlp_param_count(n_in: int, n_out: int) -> int:

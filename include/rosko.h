@@ -128,6 +128,7 @@ const char* rosko_status_string(rosko_status s);
  *                q = clamp(rint(a/s_i), -127, 127), mask = q != 0) or from I8
  *                (row_scale_dev gives the scales, NULL = all 1);
  *           F64  from F32 (exact widening; FP64 check mode).
+ * Limits: at most 65535 panels (M <= 65535 * m_r) and M * K < 2^31.
  * row_scale_dev  I8-from-I8 only: M FP32 row scales (device), else NULL.
  * tile    only tile->m_r and, for BF16, tile->dense_split_pm (minimum tile
  *         density, per mille, for keeping a dense copy; <= 0: 1 per mille)
@@ -318,10 +319,12 @@ rosko_status rosko_mlp_forward(const float* params_dev, const float* X_dev, int6
 rosko_status rosko_mlp_loss_grad(const float* params_dev, const float* X_dev, const float* Y_dev,
                                  int64_t batch, int32_t n_in, int32_t n_out, float* grads_dev,
                                  float* loss_dev, float* workspace_dev, rosko_stream_t stream);
-/* One Adam step (bias-corrected, step >= 1) on n parameters in place. */
+/* One Adam step (bias-corrected, step >= 1) on n parameters in place, of
+ * the objective L + (weight_decay / 2) |params|^2 (the step uses the
+ * gradient grads + weight_decay * params). */
 rosko_status rosko_mlp_adam(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev,
                             int64_t n, int32_t step, float lr, float beta1, float beta2,
-                            float eps, rosko_stream_t stream);
+                            float eps, float weight_decay, rosko_stream_t stream);
 /* Install trained selector weights (host array, n_in = 16, n_out =
  * rosko_num_candidates()) with the feature standardisation (mean, std) and
  * the training range [lo, hi] per feature; ROSKO_SCHED_LEARNED then picks the

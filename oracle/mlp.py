@@ -75,10 +75,13 @@ def loss_and_grad(params, X, Y):
     return loss, grads
 
 
-def adam_step(params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One Adam update (step number t >= 1).  Returns new (params, m, v)."""
+def adam_step(params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+              weight_decay=0.0):
+    """One Adam update (step number t >= 1) of the objective L + (wd/2)|p|^2,
+    whose gradient is g + wd * p.  Returns new (params, m, v)."""
     out_p, out_m, out_v = [], [], []
     for p, g, mm, vv in zip(params, grads, m, v):
+        g = g + weight_decay * p
         mm = beta1 * mm + (1 - beta1) * g
         vv = beta2 * vv + (1 - beta2) * g * g
         mhat = mm / (1 - beta1 ** t)

@@ -793,11 +793,11 @@ rosko_status rosko_mlp_loss_grad(const float* params_dev, const float* X_dev, co
 
 rosko_status rosko_mlp_adam(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev,
                             int64_t n, int32_t step, float lr, float beta1, float beta2,
-                            float eps, rosko_stream_t stream) {
-  if (!params_dev || !grads_dev || !m_dev || !v_dev || n < 1 || step < 1)
+                            float eps, float weight_decay, rosko_stream_t stream) {
+  if (!params_dev || !grads_dev || !m_dev || !v_dev || n < 1 || step < 1 || !(weight_decay >= 0))
     return ROSKO_ERR_INVALID_ARG;
   return mlp_adam(params_dev, grads_dev, m_dev, v_dev, n, step, lr, beta1, beta2, eps,
-                  static_cast<cudaStream_t>(stream));
+                  weight_decay, static_cast<cudaStream_t>(stream));
 }
 
 rosko_status rosko_selector_set(const float* params_host, int64_t n_params, const double* mean16,

@@ -195,7 +195,7 @@ rosko_status mlp_loss_grad(const float* params, const float* X, const float* Y, 
                            int n_in, int n_out, float* grads, float* loss, float* ws,
                            cudaStream_t st);
 rosko_status mlp_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
-                      float b1, float b2, float eps, cudaStream_t st);
+                      float b1, float b2, float eps, float wd, cudaStream_t st);
 rosko_status selector_set(const float* params, int n_params, int n_out, const double* mean,
                           const double* stdv, const double* lo, const double* hi);
 float time_tile(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N, int64_t ldb,

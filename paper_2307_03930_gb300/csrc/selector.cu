@@ -167,10 +167,10 @@ __global__ void dense_xgrad_kernel(const float* __restrict__ W, const float* __r
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
                             float* __restrict__ m, float* __restrict__ v, int64_t n, float lr,
-                            float b1, float b2, float eps, float c1, float c2) {
+                            float b1, float b2, float eps, float c1, float c2, float wd) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float gi = g[i];
+  const float gi = g[i] + wd * p[i];   // gradient of L + (wd / 2) |p|^2
   const float mi = b1 * m[i] + (1.0f - b1) * gi;
   const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
   m[i] = mi;
@@ -251,10 +251,10 @@ rosko_status mlp_loss_grad(const float* params, const float* X, const float* Y, 
 }
 
 rosko_status mlp_adam(float* p, const float* g, float* m, float* v, int64_t n, int step, float lr,
-                      float b1, float b2, float eps, cudaStream_t st) {
+                      float b1, float b2, float eps, float wd, cudaStream_t st) {
   const float c1 = 1.0f - powf(b1, (float)step);
   const float c2 = 1.0f - powf(b2, (float)step);
-  adam_kernel<<<blocks_for(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+  adam_kernel<<<blocks_for(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2, wd);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
 }

@@ -91,7 +91,7 @@ def lib() -> ctypes.CDLL:
         "rosko_mlp_forward": (ci, [vp, vp, i64, i32, i32, vp, vp, vp]),
         "rosko_mlp_loss_grad": (ci, [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp]),
         "rosko_mlp_adam": (ci, [vp, vp, vp, vp, i64, i32, ctypes.c_float, ctypes.c_float,
-                                ctypes.c_float, ctypes.c_float, vp]),
+                                ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]),
         "rosko_selector_set": (ci, [ctypes.POINTER(ctypes.c_float), i64] +
                                [ctypes.POINTER(ctypes.c_double)] * 4),
         "rosko_spmm_batched": (ci, [i32, vp, vp, vp, vp, vp, vp, ci, ci, ci, P_tile, vp]),
@@ -343,9 +343,10 @@ def rosko_mlp_loss_grad(params: torch.Tensor, X: torch.Tensor, Y: torch.Tensor,
 
 
 def rosko_mlp_adam(params, grads, m, v, step: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
-                   stream=None):
+                   weight_decay=0.0, stream=None):
     _check(lib().rosko_mlp_adam(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(),
-                                step, lr, beta1, beta2, eps, ctypes.c_void_p(_stream(stream))),
+                                step, lr, beta1, beta2, eps, weight_decay,
+                                ctypes.c_void_p(_stream(stream))),
            "rosko_mlp_adam")
 
 

@@ -82,7 +82,8 @@ def test_loss_and_gradients_match_oracle(soft):
         assert np.max(np.abs(a - b)) <= 1e-4 * max(1e-3, np.max(np.abs(b))), np.max(np.abs(a - b))
 
 
-def test_adam_matches_oracle():
+@pytest.mark.parametrize("wd", [0.0, 0.5])
+def test_adam_matches_oracle(wd):
     rosko = built()
     rng = np.random.default_rng(2)
     n = 1000
@@ -94,10 +95,10 @@ def test_adam_matches_oracle():
     # hyper-parameters exactly representable in FP32, so that both sides use
     # the same beta values (1 - beta is then exact in FP32 as well)
     b1, b2, lr = float(np.float32(0.9)), float(np.float32(0.999)), float(np.float32(3e-3))
-    rosko.rosko_mlp_adam(tp, tg, tm, tv, step=7, lr=lr, beta1=b1, beta2=b2)
+    rosko.rosko_mlp_adam(tp, tg, tm, tv, step=7, lr=lr, beta1=b1, beta2=b2, weight_decay=wd)
     (rp,), (rm,), (rv,) = omlp.adam_step([p.astype(np.float64)], [g.astype(np.float64)],
                                          [m.astype(np.float64)], [v.astype(np.float64)], t=7,
-                                         lr=lr, beta1=b1, beta2=b2)
+                                         lr=lr, beta1=b1, beta2=b2, weight_decay=wd)
     assert np.allclose(tp.cpu().numpy(), rp, rtol=1e-5, atol=1e-6)
     assert np.allclose(tm.cpu().numpy(), rm, rtol=1e-5, atol=1e-7)
     assert np.allclose(tv.cpu().numpy(), rv, rtol=1e-5, atol=1e-9)

@@ -71,6 +71,16 @@ def test_adam_first_step_is_lr_times_sign():
     assert np.allclose(m[0], 0.1 * g[0]) and np.allclose(v[0], 0.001 * g[0] ** 2)
 
 
+def test_adam_weight_decay_is_the_l2_gradient():
+    # decay alone (zero loss gradient): the first step moves each parameter
+    # by lr against its own sign, and m holds (1 - beta1) * wd * p
+    p = [np.array([1.0, -2.0, 0.0])]
+    z = [np.zeros(3)]
+    newp, m, _ = mlp.adam_step(p, z, z, z, t=1, lr=0.01, eps=1e-12, weight_decay=0.5)
+    assert np.allclose(newp[0], [0.99, -1.99, 0.0], atol=1e-9)
+    assert np.allclose(m[0], 0.1 * 0.5 * p[0])
+
+
 def test_training_reduces_loss():
     params, X, Y = _problem(seed=7, B=32)
     m = [np.zeros_like(p) for p in params]

@@ -164,7 +164,14 @@ def src_sha(src_files):
     return h.hexdigest()
 
 
-KERNEL_SRC = ["paper_2307_03930_gb300/csrc/spmm_sparse.cu", "paper_2307_03930_gb300/csrc/common.cuh"]
+# sources whose hash keys a committed DRAM-traffic figure (profiles/traffic.json)
+KERNEL_SRC = {
+    "dense_panel_kernel": ["paper_2307_03930_gb300/csrc/spmm_dense_tc.cu",
+                           "paper_2307_03930_gb300/csrc/tc_common.cuh",
+                           "paper_2307_03930_gb300/csrc/common.cuh"],
+    "rowdirect_kernel": ["paper_2307_03930_gb300/csrc/spmm_sparse.cu",
+                         "paper_2307_03930_gb300/csrc/common.cuh"],
+}
 
 
 # ----------------------------------------------------------------------------
@@ -266,11 +273,22 @@ def main():
     nnz = [i["nnz"] for i in infos]
     flops_step = sum(2.0 * z * N for z in nnz)
     stream = torch.cuda.current_stream()
+    # schedule: the learned selector when its trained weights are present
+    # (its choice is made and cached per handle on the first, untimed call),
+    # else the analytic rule
+    tile, form = None, "analytic tile"
+    try:
+        from paper_2307_03930_gb300 import selector as sel
+        if os.path.exists(sel.WEIGHTS):
+            sel.install()
+            tile, form = rosko.make_tile(mode=rosko.SCHED_LEARNED), "learned tile (MLP selector)"
+    except Exception as e:  # pragma: no cover - weights unreadable: analytic
+        print(f"selector not installed: {e}", file=sys.stderr)
 
-    def step(t, hs=handles16, key="B16"):
+    def step(t, hs=handles16, key="B16", tl=None):
         S = sets[t % 2]
         for i in range(len(SPARSITIES)):
-            rosko.rosko_spmm(hs[i], S[key][i], S["C"][i])
+            rosko.rosko_spmm(hs[i], S[key][i], S["C"][i], tile=tl if tl is not None else tile)
 
     for t in range(args.warmup):
         step(t)
@@ -307,10 +325,19 @@ def main():
     # distinct B buffers of one input set (~174 MB, > L2) so no call finds
     # its B in L2
     per_kernel_ms = [cycled_time(lambda j, i=i: rosko.rosko_spmm(
-        handles16[i], sets[0]["B16"][j], sets[0]["C"][j]), torch) for i in range(len(SPARSITIES))]
+        handles16[i], sets[0]["B16"][j], sets[0]["C"][j], tile=tile), torch)
+        for i in range(len(SPARSITIES))]
     ms_step = elapsed_ms / args.steps
     value = job_value(flops_step, args.steps, world, elapsed_ms)
     status = rosko.rosko_device_status(clear=True)
+    # which kernel each SpMM runs (the library's own plan of the call)
+    plans = [rosko.rosko_spmm_plan(handles16[i], sets[0]["B16"][i], sets[0]["C"][i], tile=tile)
+             for i in range(len(SPARSITIES))]
+    # the same step under the analytic rule, for the learned-vs-analytic gain
+    analytic_step_ms = None
+    if tile is not None:
+        analytic_step_ms = graph_time(lambda: step(0, tl=rosko.make_tile()), torch, reps=20)
+    learned_step_ms = graph_time(lambda: step(0), torch, reps=20)
 
     # ---------------- per-sparsity figures and the roofline -------------------
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -320,26 +347,50 @@ def main():
         inf = infos[i]
         bytes_alg = inf["bytes"] + inf["touched_k"] * N * 2 + M * N * 4
         t = per_kernel_ms[i] * 1e-3
-        per.append({"sparsity": s, "nnz": nnz[i], "ms": per_kernel_ms[i],
-                    "gflops": 2.0 * nnz[i] * N / t / 1e9, "alg_bytes": bytes_alg,
+        pl = plans[i]
+        kern = ("dense_panel_kernel" if pl["sparse_panels"] == 0 else
+                "rowdirect_kernel" if pl["dense_tiles"] == 0 else "dense_panel+rowdirect")
+        if pl["dense_tiles"] == 0 and pl["order"] != 4:
+            kern = f"sparse_spmm_kernel(order {pl['order']})"
+        per.append({"sparsity": s, "nnz": nnz[i], "ms": per_kernel_ms[i], "kernel": kern,
+                    "plan": pl, "gflops": 2.0 * nnz[i] * N / t / 1e9, "alg_bytes": bytes_alg,
                     "hbm_gbs": bytes_alg / t / 1e9,
-                    "hbm_frac": bytes_alg / t / 1e9 / pk["hbm_gbs"],
-                    "alu_frac": 2.0 * nnz[i] * N / t / 1e12 / fp32_peak_tflops})
-    dom = max(range(len(per)), key=lambda i: per[i]["ms"])
-    d = per[dom]
-    t_alu = 2.0 * d["nnz"] * N / (fp32_peak_tflops * 1e12)
-    t_hbm = d["alg_bytes"] / (pk["hbm_gbs"] * 1e9)
-    if t_alu >= t_hbm:
-        roof = {"bound": "alu", "achieved": d["gflops"] / 1e3, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": d["gflops"] / 1e3 / fp32_peak_tflops}
+                    "hbm_frac": bytes_alg / t / 1e9 / pk["hbm_gbs"]})
+    # the dominant kernel: largest share of the per-kernel time of a step
+    kinds = {}
+    for r in per:
+        k = kinds.setdefault(r["kernel"], {"launches_per_step": 0, "ms": 0.0, "alg_bytes": 0.0,
+                                           "alg_flops": 0.0})
+        k["launches_per_step"] += 1
+        k["ms"] += r["ms"]
+        k["alg_bytes"] += r["alg_bytes"]
+        k["alg_flops"] += 2.0 * r["nnz"] * N
+    tot_ms = sum(k["ms"] for k in kinds.values())
+    for k in kinds.values():
+        k["share"] = k["ms"] / tot_ms
+    dom_name = max(kinds, key=lambda k: kinds[k]["ms"])
+    dk = kinds[dom_name]
+    # bound: whichever of algorithmic bytes at HBM peak and algorithmic flops
+    # at the kernel's arithmetic peak takes longer
+    arith_peak = pk["bf16_tflops"] if dom_name.startswith("dense") else fp32_peak_tflops
+    t_arith = dk["alg_flops"] / (arith_peak * 1e12)
+    t_hbm = dk["alg_bytes"] / (pk["hbm_gbs"] * 1e9)
+    sec = dk["ms"] * 1e-3
+    if t_arith > t_hbm:
+        roof = {"bound": "tensor" if dom_name.startswith("dense") else "alu",
+                "achieved": dk["alg_flops"] / sec / 1e12, "peak": arith_peak, "unit": "TFLOP/s"}
     else:
-        roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": d["hbm_gbs"] / pk["hbm_gbs"]}
-    key = f"sparse_bf16_s{int(round(SPARSITIES[dom] * 1000))}"
-    roof["traffic"] = traffic_for(key, KERNEL_SRC)
-    roof["kernel"] = f"sparse_spmm_kernel<bf16> at {SPARSITIES[dom] * 100:g}% sparsity"
-    roof["peak_source"] = pk["source"] if roof["bound"] == "hbm" else (
-        f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz")
+        roof = {"bound": "hbm", "achieved": dk["alg_bytes"] / sec / 1e9, "peak": pk["hbm_gbs"],
+                "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_for(dom_name, KERNEL_SRC.get(dom_name, []))
+    roof["kernel"] = dom_name
+    roof["launches_per_step"] = dk["launches_per_step"]
+    roof["per_launch_ms"] = dk["ms"] / dk["launches_per_step"]
+    roof["alg_bytes_per_launch"] = dk["alg_bytes"] / dk["launches_per_step"]
+    roof["peak_source"] = (f"{pk['source']} (MEASURED_PEAKS.json)" if roof["bound"] in ("hbm", "tensor")
+                           else f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
+                                f"{pk['sm_max_mhz']:.0f} MHz")
 
     extras = {}
     if not args.no_extras:
@@ -347,19 +398,22 @@ def main():
         extras["batched_uneven_layers"] = batched_leg(rosko, torch, dev)
 
     # ---------------- end to end: host buffers through the C-ABI -----------------
-    e2e = end_to_end(rosko, torch, dev, sets, handles16, stream, flops_step, world)
+    e2e = end_to_end(rosko, torch, dev, sets, handles16, stream, flops_step, world, tile=tile)
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "BF16 A and B, FP32 accumulate, analytic tile",
+            "config": {"workload": WORKLOAD, "form": f"BF16 A and B, FP32 accumulate, {form}",
                        "l2": f"inputs alternate between 2 sets of {2 * 6 * K * N * 2 / 1e6:.0f} MB "
                              "of BF16 B (> 129 MB L2), no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "device_status": status,
-            "per_sparsity": per, "comparisons": extras}
+            "kernels": kinds, "per_sparsity": per,
+            "schedule": {"form": form, "step_ms_graph": learned_step_ms,
+                         "analytic_step_ms_graph": analytic_step_ms},
+            "comparisons": extras}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -562,7 +616,7 @@ def batched_leg(rosko, torch, dev, seed=3, count=64):
     return out
 
 
-def end_to_end(rosko, torch, dev, sets, handles, stream, flops_step, world, steps=50):
+def end_to_end(rosko, torch, dev, sets, handles, stream, flops_step, world, steps=50, tile=None):
     """Same metric through the C-ABI with pinned host buffers: per step the six
     B inputs are copied host->device, the SpMMs run, and the six C results are
     copied back (the packed weights stay resident, as for pre-packed inference
@@ -575,7 +629,7 @@ def end_to_end(rosko, torch, dev, sets, handles, stream, flops_step, world, step
     def one(t):
         for i in range(len(SPARSITIES)):
             dB[i].copy_(hB[t % 2][i], non_blocking=True)
-            rosko.rosko_spmm(handles[i], dB[i], dC[i])
+            rosko.rosko_spmm(handles[i], dB[i], dC[i], tile=tile)
             hC[i].copy_(dC[i], non_blocking=True)
 
     for t in range(3):

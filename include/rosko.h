@@ -166,6 +166,29 @@ rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype
                         rosko_dtype c_dtype, int64_t ldc, int accumulate,
                         const rosko_tile* tile, rosko_stream_t stream);
 
+/* The work split one rosko_spmm call runs (see rosko_spmm_plan). */
+typedef struct {
+  int64_t dense_tiles;    /* 128-row tiles on the tensor-core path            */
+  int64_t sparse_panels;  /* m_r-row panels on the CUDA-core path             */
+  int32_t order;          /* CUDA-core traversal (1..4), 0 when no panel      */
+  int32_t zero_fill;      /* 1 when C is zero-filled before the kernels       */
+  rosko_tile tile;        /* the schedule resolved for the call               */
+} rosko_plan;
+
+/*
+ * rosko_spmm_plan - what rosko_spmm with the same arguments would run,
+ * without running it: the split between the tensor-core and CUDA-core
+ * paths, the traversal and the resolved tile.  Arguments are validated as in
+ * rosko_spmm; nothing is written to C.  In ROSKO_SCHED_LEARNED mode without
+ * a cached choice the selector's feature kernels run (and synchronise), in
+ * ROSKO_SCHED_AUTOTUNE mode without a cached choice the autotuner runs (and
+ * writes C); both cache their choice on the handle as rosko_spmm does.
+ */
+rosko_status rosko_spmm_plan(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                             int64_t ldb, const float* col_scale_dev, void* C_dev,
+                             rosko_dtype c_dtype, int64_t ldc, int accumulate,
+                             const rosko_tile* tile, rosko_plan* out, rosko_stream_t stream);
+
 /*
  * rosko_spmm_batched - C_i = A_i . B_i (or C_i += ...) for `count` <= 64
  * independent problems (pruned layers of different shapes).  The dense-panel tiles of

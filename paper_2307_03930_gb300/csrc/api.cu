@@ -99,19 +99,28 @@ CUresult encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank,
   return g_encode(map, dt, rank, gaddr, dims, strides, box, estrides, il, sw, l2, oob);
 }
 
-// Rows per tensor-core CTA tile by default (128 or 256).
-constexpr int kDenseMc = 128;
-
-// Tensor-core dense-panel tiles: the stream-K kernel spreads the work over one
-// CTA per SM whatever the tile count, so only the CTA width matters: 256 halves
-// the L2->SM traffic of A (read once per column tile) against 128.
+// Tensor-core dense-panel tiles (measured on GB300, stream-K kernel):
+//  * K of fewer than 16 slabs (K < 1024): cutting tiles along K buys little
+//    and costs a zero fill of C and reduce-adds, so every tile is owned whole
+//    by one CTA; 128-wide tiles give more of them;
+//  * otherwise one CTA per SM shares the (tile, slab) units; 256 columns per
+//    tile halve the L2->SM traffic of A against 128, and 256 rows (two MMAs
+//    on one B stage) pay off once there are 16 or more 128-row tiles (a
+//    4096 x 4096 x 4096 layer: 100 us against 105 us; a 512-row layer runs
+//    faster with 128 rows: 23 us against 29 us).
 void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, int* ctas_out,
                   int* mc_out) {
-  (void)n_tiles;
-  (void)K;
+  const int64_t slabs = (K + 63) / 64;
+  if (slabs < 16) {
+    const int64_t tiles = n_tiles * ((N + 127) / 128);
+    *TN_out = 128;
+    *mc_out = 128;
+    *ctas_out = (int)std::max<int64_t>(1, tiles <= 65535 ? tiles : sms);
+    return;
+  }
   *TN_out = N > 128 ? 256 : 128;
+  *mc_out = n_tiles >= 16 ? 256 : 128;
   *ctas_out = sms;
-  *mc_out = kDenseMc;
 }
 
 // Density (per mille) from which a 128-row tile runs on the tensor cores.
@@ -143,11 +152,13 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
                                rosko_dtype dt, int sms, rosko_tile* t) {
   if (m_r <= 0) m_r = 16;
   const double d = (M * K > 0) ? (double)nnz / ((double)M * (double)K) : 0.0;
-  // Traversal: row-slot (no run-time register indexing, needs 16-bit k).
-  // Below ~5% density a 128-row tile leaves many B rows untouched
-  // ((1-d)^128 of them), so the tile gathers only the rows its panels touch.
-  int order = K < kRowSlotMaxK ? 2 : 1;
-  if (order == 2 && m_r == 16 && d < 0.05) order = 3;
+  // Traversal: row-direct (each C row walks its own nonzeros, k ascending,
+  // and reads their B rows straight from L2; needs the 16-bit-k row stream).
+  // A staged B slab pays only when many of a CTA's rows use its rows, and
+  // From 50% to 99.8% sparsity (512 x 4608 x 3136, FP32 and BF16) it is in
+  // fact 3-4x faster than the slab orders everywhere, so it is the default
+  // whenever the row stream exists (K < 65280).
+  int order = K < kRowSlotMaxK ? 4 : 1;
   const int V = sparse_default_V(dt, m_r, order);
   const int NR = 32 * V;
   const int64_t P = (M + m_r - 1) / m_r;
@@ -173,6 +184,17 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
   t->m_c = W * m_r;
   t->split_k = (int32_t)split;
   t->dense_split_pm = (dt == ROSKO_BF16) ? kDenseSplitPm : 1001;
+  if (dt == ROSKO_BF16 && order == 4) {
+    // Small layers: the tensor-core launch has a fixed cost (~6 us: set-up,
+    // the first cold loads, the epilogue) that row-direct (~3 us) does not.
+    // Model both on the uniform-density assumption (every tile dense at
+    // d >= 5 per mille) and keep the layer sparse when row-direct is
+    // predicted faster: dense work at ~0.8 PFLOP/s, row-direct moving
+    // nnz * N BF16 values from L2 at ~5 TB/s.
+    const double t_dense = 6.0 + 2.0 * (double)M * (double)K * (double)N / 0.8e15 * 1e6;
+    const double t_direct = 3.0 + (double)nnz * (double)N * 2.0 / 5e12 * 1e6;
+    if (t_direct < t_dense) t->dense_split_pm = 1001;
+  }
   int TN = 256, ds = 1;
   int mc = 128;
   dense_config((M + 127) / 128, N, K, sms, &TN, &ds, &mc);
@@ -250,6 +272,7 @@ void rosko_free(rosko_packed_t A) {
   if (A->dense_base) cudaFree(A->dense_base);
   if (A->row_base) cudaFree(A->row_base);
   if (A->gather_base) cudaFree(A->gather_base);
+  if (A->seg_base) cudaFree(A->seg_base);
   delete A;
 }
 
@@ -311,6 +334,9 @@ rosko_status spmm_validate(rosko_packed_s* A, const void* B_dev, rosko_dtype b_d
 
 // Resolve the tile (fields <= 0 take the analytic rule) and launch the dense
 // and sparse paths.  Arguments were validated by spmm_validate.
+// Output of a plan-only run (kRunPlanOnly), per calling thread.
+thread_local rosko_plan* g_plan_out = nullptr;
+
 rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
                       int64_t ldb, const float* col_scale_dev, void* C_dev, rosko_dtype c_dtype,
                       int64_t ldc, int accumulate, const rosko_tile* tile, cudaStream_t st,
@@ -374,7 +400,21 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
   L.KC = t.k_c;
   L.split = t.split_k;
   L.order = t.order;
-  if (L.order < 1 || L.order > 3) return ROSKO_ERR_INVALID_ARG;
+  if (L.order < 1 || L.order > 4) return ROSKO_ERR_INVALID_ARG;
+  if (L.order == 4 && !(A->rnz && sparse_config_supported(p, b_dtype, c_dtype, L.R, L.V, 4))) {
+    // no row stream (K >= 65280) or no row-direct variant: column order
+    if (tile && tile->order == 4) return ROSKO_ERR_UNSUPPORTED;
+    L.order = 1;
+    L.V = sparse_default_V(p, A->m_r, 1);
+    if (t.k_c < 8) t.k_c = 32;
+    L.KC = t.k_c;
+  }
+  if (L.order == 4) {
+    // one warp per C row, B from L2: no slabs, no K split
+    L.W = 1;
+    L.split = 1;
+    L.KC = 8;
+  }
   if (L.order == 3 && (!A->gnz || A->m_r != 16)) {
     if (tile && tile->order == 3) return ROSKO_ERR_UNSUPPORTED;
     L.order = 2;
@@ -402,15 +442,37 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
   // B ring: up to 4 slabs, at least 2, within ~200 KB of shared memory
   const size_t stage_bytes = (size_t)L.KC * 32 * L.V * bsz;
   L.stages = (int)std::min<size_t>(4, (200 * 1024) / stage_bytes);
+  if (L.order == 4) L.stages = 2;   // unused
   if (L.stages < 2) return ROSKO_ERR_INVALID_ARG;
 
   // one zero fill of C serves every kernel that adds partial sums atomically
   const bool skip_dense = (flags & kRunSkipDense) != 0;
+  bool direct_cut = false;
+  if (L.order == 4 && n_sparse > 0) {
+    int64_t ns = 0;
+    if (!direct_segments(A, A->panel_order_dev, n_sparse, &ns, &direct_cut))
+      return ROSKO_ERR_UNSUPPORTED;
+  }
   const bool zero_c =
-      !accumulate && ((n_sparse > 0 && L.split > 1) ||
+      !accumulate && ((n_sparse > 0 && (L.split > 1 || direct_cut)) ||
                       (!skip_dense && n_dense > 0 &&
                        dense_needs_zero(n_dense, N, A->K, t.dense_n_r, t.dense_split_k,
                                         t.dense_m_c / 128)));
+  if (flags & kRunPlanOnly) {
+    // report the split and the resolved schedule, launch nothing
+    rosko_plan* out = g_plan_out;
+    if (out) {
+      out->dense_tiles = skip_dense ? 0 : n_dense;
+      out->sparse_panels = n_sparse;
+      out->order = n_sparse > 0 ? L.order : 0;
+      out->zero_fill = zero_c ? 1 : 0;
+      out->tile = t;
+      out->tile.order = L.order;
+      out->tile.n_r = 32 * L.V;
+      out->tile.split_k = L.split;
+    }
+    return ROSKO_OK;
+  }
   if (zero_c && !(flags & kRunZeroed) &&
       cudaMemset2DAsync(C_dev, (size_t)ldc * csz, 0, (size_t)N * csz, (size_t)A->M, st) !=
           cudaSuccess)
@@ -463,8 +525,9 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
   std::vector<int> job_of;        // problem index of each dense job
   std::vector<rosko_tile> rest;   // per problem: tile for the sparse remainder
   std::vector<char> active((size_t)count, 0), dense_any((size_t)count, 0);
+  std::vector<char> direct_cut((size_t)count, 0);
   rest.resize((size_t)count);
-  int TN = 128, MH = kDenseMc / 128;
+  int TN = 128, MH = 1;   // one launch serves every shape: 128-row tiles
   if (tiles)
     for (int32_t i = 0; i < count; ++i)
       if (tiles[i].dense_m_c > 0) {
@@ -513,6 +576,14 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
     rosko_tile r = tiles ? tiles[i] : t;
     r.dense_split_pm = t.dense_split_pm;
     if (r.split_k <= 0) r.split_k = t.split_k;
+    if ((r.order > 0 ? r.order : t.order) == 4) {
+      r.split_k = 1;   // row-direct: no K split, but cut rows add into C
+      int64_t ns = 0;
+      bool cut = false;
+      if (A[i]->rnz && direct_segments(A[i], A[i]->panel_order_dev, A[i]->P - dp, &ns, &cut) &&
+          cut)
+        direct_cut[(size_t)i] = 1;
+    }
     rest[(size_t)i] = r;
     // whole-dense problems need no sparse launch
     if (dp == A[i]->P) rest[(size_t)i].m_r = -1;
@@ -530,7 +601,8 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
     }
     for (int32_t i = 0; i < count; ++i) {
       if (!active[(size_t)i]) continue;
-      if (rest[(size_t)i].m_r != -1 && rest[(size_t)i].split_k > 1) need[(size_t)i] = 1;
+      if (rest[(size_t)i].m_r != -1 && (rest[(size_t)i].split_k > 1 || direct_cut[(size_t)i]))
+        need[(size_t)i] = 1;
       if (!need[(size_t)i]) continue;
       const size_t csz = dtype_size(c_dt);
       if (cudaMemset2DAsync(C[i], (size_t)ldc[i] * csz, 0, (size_t)N[i] * csz, (size_t)A[i]->M,
@@ -543,9 +615,35 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
     rosko_status s = dense_batch_launch(jobs.data(), (int)jobs.size(), TN, sms, MH, st);
     if (s != ROSKO_OK) return s;
   }
-  // sparse remainders (the dense tiles were launched above)
+  // sparse remainders (the dense tiles were launched above): the row-direct
+  // ones (order 4, one V) share one launch, the others run one per problem
+  std::vector<DirectJob> direct;
+  std::vector<char> in_direct((size_t)count, 0);
+  int direct_V = 0;
   for (int32_t i = 0; i < count; ++i) {
     if (!active[(size_t)i] || rest[(size_t)i].m_r == -1) continue;
+    const rosko_tile& r = rest[(size_t)i];
+    rosko_tile t{};
+    schedule_analytic(A[i]->M, A[i]->K, N[i], A[i]->nnz, A[i]->m_r, A[i]->dt, sms, &t);
+    const int ord = r.order > 0 ? r.order : t.order;
+    if (ord != 4 || !A[i]->rnz) continue;
+    const int V = r.n_r > 0 ? r.n_r / 32 : sparse_default_V(A[i]->dt, A[i]->m_r, 4);
+    if (!sparse_config_supported(A[i]->dt, b_dt, c_dt, A[i]->m_r, V, 4)) continue;
+    if (direct_V != 0 && V != direct_V) continue;
+    int64_t nd = 0, dp = 0;
+    dense_prefix(A[i], r.dense_split_pm, &nd, &dp);
+    DirectJob j{A[i], B[i], b_dt, N[i], ldb[i], nullptr, C[i], c_dt, ldc[i], accumulate,
+                A[i]->panel_order_dev, A[i]->P - dp};
+    direct.push_back(j);
+    direct_V = V;
+    in_direct[(size_t)i] = 1;
+  }
+  if (!direct.empty()) {
+    rosko_status s = direct_batch_launch(direct.data(), (int)direct.size(), direct_V, st);
+    if (s != ROSKO_OK) return s;
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    if (!active[(size_t)i] || rest[(size_t)i].m_r == -1 || in_direct[(size_t)i]) continue;
     rosko_tile r = rest[(size_t)i];
     r.m_r = 0;
     const int flags = kRunSkipDense | (zeroed[(size_t)i] ? kRunZeroed : 0);
@@ -559,10 +657,10 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
 
 extern "C" {
 
-rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
-                        int64_t ldb, const float* col_scale_dev, void* C_dev,
-                        rosko_dtype c_dtype, int64_t ldc, int accumulate,
-                        const rosko_tile* tile, rosko_stream_t stream) {
+static rosko_status spmm_dispatch(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype,
+                                  int64_t N, int64_t ldb, const float* col_scale_dev, void* C_dev,
+                                  rosko_dtype c_dtype, int64_t ldc, int accumulate,
+                                  const rosko_tile* tile, rosko_stream_t stream, int flags) {
   bool done = false;
   rosko_status v = spmm_validate(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc,
                                  accumulate, static_cast<cudaStream_t>(stream), &done);
@@ -598,14 +696,35 @@ rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype
         A->sched_cache[N * 4 + mode] = chosen;
       }
       return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,
-                      &chosen, st, 0);
+                      &chosen, st, flags);
     }
     // no cached choice and none can be made here: the analytic rule
     return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,
-                    nullptr, st, 0);
+                    nullptr, st, flags);
   }
   return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate, tile,
-                  st, 0);
+                  st, flags);
+}
+
+rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                        int64_t ldb, const float* col_scale_dev, void* C_dev,
+                        rosko_dtype c_dtype, int64_t ldc, int accumulate,
+                        const rosko_tile* tile, rosko_stream_t stream) {
+  return spmm_dispatch(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,
+                       tile, stream, 0);
+}
+
+rosko_status rosko_spmm_plan(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
+                             int64_t ldb, const float* col_scale_dev, void* C_dev,
+                             rosko_dtype c_dtype, int64_t ldc, int accumulate,
+                             const rosko_tile* tile, rosko_plan* out, rosko_stream_t stream) {
+  if (!out) return ROSKO_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  g_plan_out = out;
+  const rosko_status s = spmm_dispatch(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype,
+                                       ldc, accumulate, tile, stream, kRunPlanOnly);
+  g_plan_out = nullptr;
+  return s;
 }
 
 rosko_status rosko_unpack(rosko_packed_t A, void* A_dev_out, int64_t lda, rosko_stream_t stream) {

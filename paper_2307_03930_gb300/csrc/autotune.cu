@@ -17,14 +17,15 @@ namespace rosko {
 namespace {
 
 struct SparseCand {
-  int order, W, KC, split;
+  int order, W, KC, split, V;   // V = 0: the order's default width
 };
 
-// Sparse-path configurations (m_r comes from the pack, n_r from the order).
+// Sparse-path configurations (m_r comes from the pack, n_r from the order
+// unless V is given).
 const SparseCand kSparse[] = {
-    {2, 4, 64, 1}, {2, 4, 64, 4}, {2, 8, 32, 2}, {2, 8, 128, 1},
-    {3, 8, 64, 1}, {3, 8, 128, 2}, {3, 8, 128, 4}, {3, 8, 256, 8},
-    {1, 4, 64, 1}, {1, 8, 32, 4},
+    {2, 4, 64, 1, 0}, {2, 4, 64, 4, 0}, {2, 8, 32, 2, 0}, {2, 8, 128, 1, 0},
+    {3, 8, 64, 1, 0}, {3, 8, 128, 2, 0}, {3, 8, 128, 4, 0}, {3, 8, 256, 8, 0},
+    {1, 4, 64, 1, 0}, {1, 8, 32, 4, 0}, {4, 1, 8, 1, 4}, {4, 1, 8, 1, 8},
 };
 constexpr int kNumSparse = sizeof(kSparse) / sizeof(kSparse[0]);
 // Dense-split thresholds in per mille (1001 = never).
@@ -43,9 +44,15 @@ bool candidate_tile(const rosko_packed_s* h, int64_t N, int idx, rosko_tile* t) 
   const SparseCand& sc = kSparse[idx / kNumDense];
   const int dpct = kDensePm[idx % kNumDense];
   if (sc.order == 3 && (!h->gnz || h->m_r != 16)) return false;
-  if (sc.order == 2 && !h->rnz) return false;
+  if ((sc.order == 2 || sc.order == 4) && !h->rnz) return false;
   if (dpct <= 1000 && !(h->dt == ROSKO_BF16 && h->n_copy > 0)) return false;
-  const int V = sparse_default_V(h->dt, h->m_r, sc.order);
+  const int V = sc.V > 0 ? sc.V : sparse_default_V(h->dt, h->m_r, sc.order);
+  if (sc.order == 4) {
+    // the B and C types are those of the handle's usual call
+    const rosko_dtype b = h->dt == ROSKO_F64 ? ROSKO_F32 : h->dt;
+    const rosko_dtype c = h->dt == ROSKO_I8 ? ROSKO_I32 : (h->dt == ROSKO_F64 ? ROSKO_F64 : ROSKO_F32);
+    if (!sparse_config_supported(h->dt, b, c, h->m_r, V, 4)) return false;
+  }
   const int W = sc.order == 3 ? 128 / h->m_r : sc.W;
   const size_t esz = h->dt == ROSKO_F64 ? 4 : dtype_size(h->dt);
   if (2 * (size_t)sc.KC * 32 * V * esz > 200 * 1024) return false;

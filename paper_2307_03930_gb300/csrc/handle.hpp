@@ -58,6 +58,17 @@ struct rosko_packed_s {
   int32_t* gu_k = nullptr;
   void* gnz = nullptr;
   int64_t gu_total = 0;
+  // Row-direct work segments (row stream only): each row is cut into pieces
+  // of at most kSegRecords nonzeros, {row, piece} per segment, in row order
+  // (seg_nat) and in panel_order order (seg_ord, BF16 packs with dense
+  // copies); seg_prefix[i] / split_prefix[i] count the segments / the panels
+  // with a cut row among the first i panels of panel_order (or of the
+  // natural order when there is no panel_order).
+  void* seg_base = nullptr;
+  int2* seg_nat = nullptr;
+  int2* seg_ord = nullptr;
+  std::vector<int64_t> seg_prefix;
+  std::vector<int32_t> split_prefix;
   float* feat_dev = nullptr;   // kNumFeatures floats (N-independent part)
   int64_t* panel_nnz_dev = nullptr;  // P+1 nonzero offsets of panels
   // Dense-panel split (BF16 only).  128-row tiles sorted by density,
@@ -71,6 +82,7 @@ struct rosko_packed_s {
   int32_t* tile_order_dev = nullptr;
   int32_t* panel_order_dev = nullptr;
   std::vector<int32_t> tile_order;        // host copy
+  std::vector<int32_t> panel_order_host;  // host copy of panel_order
   std::vector<double> tile_density;       // sorted, descending
   std::vector<int32_t> tile_panels;       // panels per tile (indexed by tile id)
   std::vector<int64_t> panel_nnz;         // host copy, P+1 offsets
@@ -127,6 +139,32 @@ rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t 
                                int64_t M, int accumulate, int TN, int ctas, int MH,
                                bool c_zeroed,
                                cudaStream_t st);
+// One row-direct (order 4) sparse SpMM of a batch: the panels of h listed in
+// panel_list (NULL: all rows), B and C of this problem.
+struct DirectJob {
+  rosko_packed_s* h;
+  const void* B;
+  rosko_dtype b_dt;
+  int64_t N, ldb;
+  const float* col_scale;
+  void* C;
+  rosko_dtype c_dt;
+  int64_t ldc;
+  int accumulate;
+  const int32_t* panel_list;
+  int64_t n_panels;
+};
+// Row-direct work segments of the listed panels (NULL list: all panels in
+// order; else the handle's panel_order prefix of n_panels); NULL if the list
+// is of another kind.  *cut: some listed row is cut into several pieces
+// (their sums are added into C, which must then be zeroed unless the call
+// accumulates).
+const int2* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
+                            int64_t* n_segs, bool* cut);
+// One launch over all jobs (count <= 64, same handle / B / C types, V
+// columns per lane); C of jobs with cut rows must be zeroed by the caller
+// unless they accumulate.
+rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaStream_t st);
 // One dense-panel SpMM of a batch (see dense_batch_launch).
 struct DenseJob {
   const void* dense_A;
@@ -156,8 +194,12 @@ rosko_status spmm_validate(rosko_packed_s* A, const void* B_dev, rosko_dtype b_d
                            int64_t ldb, const float* col_scale_dev, void* C_dev,
                            rosko_dtype c_dtype, int64_t ldc, int accumulate, cudaStream_t st,
                            bool* done);
+// Nonzeros per row-direct work segment (longer rows are cut and their pieces
+// added into C atomically).
+constexpr int kSegRecords = 128;
 constexpr int kRunSkipDense = 1;
 constexpr int kRunZeroed = 2;
+constexpr int kRunPlanOnly = 4;   // resolve the schedule, launch nothing (rosko_spmm_plan)
 rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
                       int64_t ldb, const float* col_scale_dev, void* C_dev, rosko_dtype c_dtype,
                       int64_t ldc, int accumulate, const rosko_tile* tile, cudaStream_t st,

@@ -683,7 +683,8 @@ rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pm, ro
     h->tile_density[(size_t)c] = dens[(size_t)h->tile_order[(size_t)c]];
     if (h->tile_density[(size_t)c] * 1000.0 >= (double)dense_min_pm) n_copy = c + 1;
   }
-  std::vector<int32_t> panel_order;
+  std::vector<int32_t>& panel_order = h->panel_order_host;
+  panel_order.clear();
   panel_order.reserve((size_t)P);
   for (int64_t c = T - 1; c >= 0; --c) {
     const int64_t t = h->tile_order[(size_t)c];
@@ -716,6 +717,56 @@ rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pm, ro
   }
   // host vectors are staged by the copies above; wait before they go away
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  return ROSKO_OK;
+}
+
+// Row-direct work segments (see rosko_packed_s): built on the host from the
+// row pointers, once per pack.
+rosko_status build_segments(rosko_packed_s* h, const std::vector<int32_t>* panel_order,
+                            cudaStream_t st) {
+  const int64_t M = h->M, P = h->P;
+  if (!h->rowptr || M == 0) return ROSKO_OK;
+  std::vector<int32_t> rp((size_t)M + 1);
+  if (cudaStreamSynchronize(st) != cudaSuccess ||
+      cudaMemcpy(rp.data(), h->rowptr, (size_t)(M + 1) * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+  std::vector<int2> nat;
+  nat.reserve((size_t)M + (size_t)(h->nnz / kSegRecords) + 1);
+  std::vector<int64_t> panel_seg((size_t)P + 1, 0);
+  std::vector<char> panel_split((size_t)P, 0);
+  for (int64_t p = 0; p < P; ++p) {
+    panel_seg[(size_t)p] = (int64_t)nat.size();
+    for (int64_t r = p * h->m_r; r < std::min<int64_t>(M, (p + 1) * h->m_r); ++r) {
+      const int64_t nr = (int64_t)rp[(size_t)r + 1] - rp[(size_t)r] - 1;   // minus the sentinel
+      const int64_t ns = std::max<int64_t>(1, (nr + kSegRecords - 1) / kSegRecords);
+      if (ns > 1) panel_split[(size_t)p] = 1;
+      for (int64_t k = 0; k < ns; ++k) nat.push_back(make_int2((int)r, (int)k));
+    }
+  }
+  panel_seg[(size_t)P] = (int64_t)nat.size();
+  std::vector<int2> ord;
+  h->seg_prefix.assign((size_t)P + 1, 0);
+  h->split_prefix.assign((size_t)P + 1, 0);
+  for (int64_t i = 0; i < P; ++i) {
+    const int64_t p = panel_order ? (*panel_order)[(size_t)i] : i;
+    if (panel_order)
+      ord.insert(ord.end(), nat.begin() + panel_seg[(size_t)p], nat.begin() + panel_seg[(size_t)p + 1]);
+    h->seg_prefix[(size_t)i + 1] = h->seg_prefix[(size_t)i] + (panel_seg[(size_t)p + 1] - panel_seg[(size_t)p]);
+    h->split_prefix[(size_t)i + 1] = h->split_prefix[(size_t)i] + panel_split[(size_t)p];
+  }
+  const size_t n = nat.size();
+  const size_t o_ord = align_up(n * sizeof(int2), 256);
+  if (dev_malloc(&h->seg_base, o_ord + (panel_order ? n * sizeof(int2) : 0) + 256) != cudaSuccess)
+    return ROSKO_ERR_OOM;
+  h->seg_nat = static_cast<int2*>(h->seg_base);
+  h->seg_ord = panel_order ? reinterpret_cast<int2*>(static_cast<char*>(h->seg_base) + o_ord)
+                           : nullptr;
+  if (cudaMemcpyAsync(h->seg_nat, nat.data(), n * sizeof(int2), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      (panel_order && cudaMemcpyAsync(h->seg_ord, ord.data(), n * sizeof(int2),
+                                      cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      cudaStreamSynchronize(st) != cudaSuccess)
     return ROSKO_ERR_CUDA;
   return ROSKO_OK;
 }
@@ -754,7 +805,10 @@ rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, in
       s = build_dense_tiles<__nv_bfloat16>((const __nv_bfloat16*)A, lda, dense_min_pm, h,
                                            stream);
   }
+  if (s == ROSKO_OK)
+    s = build_segments(h, h->panel_order_dev ? &h->panel_order_host : nullptr, stream);
   if (s != ROSKO_OK) {
+    if (h->seg_base) cudaFree(h->seg_base);
     if (h->meta_base) cudaFree(h->meta_base);
     if (h->data_base) cudaFree(h->data_base);
     if (h->dense_base) cudaFree(h->dense_base);

@@ -9,16 +9,25 @@
 // memory stages filled by TMA, one elected thread issues tcgen05.mma
 // (M = 128, N = TN, K = 16 per instruction) and C is written once.
 //
-// Warp roles (6 warps): 0 = TMA producer, 1 = MMA issuer (and TMEM owner),
-// 2..5 = epilogue (warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31).
+// Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2.. =
+// epilogue (warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31; with 8
+// epilogue warps two share a lane quarter and split its columns).
 //
 // Schedule: persistent stream-K.  The (tile, K slab) units of all dense tiles
 // are cut into one equal contiguous share per SM, so small-M problems (few
 // row tiles) still fill every SM in one wave.  A share covers the K ranges of
 // one or two tiles; two TMEM accumulators alternate so that the epilogue of
 // one range overlaps the MMAs of the next.  A tile whose K range is cut
-// between CTAs is added into C with 16-byte atomics; a tile owned whole is
-// stored.
+// between CTAs is added into C; a tile owned whole is stored.
+//
+// Epilogue: each epilogue warp moves its 32 TMEM lanes (C rows) 32 columns
+// at a time into a 32 x 32 FP32 staging tile in shared memory (128-byte
+// swizzle, so the row-per-lane writes are bank-conflict free) and one lane
+// hands the tile to TMA: a tensor store for a whole tile, a tensor
+// reduce-add (element-wise add in L2) for a cut tile or C += A.B.  Two
+// staging tiles per warp let the next chunk's TMEM load overlap the copy.
+// C whose rows are not 16-byte aligned falls back to direct stores and
+// 16-byte atomics.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -32,6 +41,16 @@ namespace {
 constexpr int kTM = 128;             // rows of a dense tile (MMA M)
 constexpr int kTK = 64;              // K per stage: 64 BF16 = one 128-byte swizzle row
 constexpr uint32_t kABytes = kTM * kTK * 2;   // 16 KB
+constexpr uint32_t kStageC = 32 * 32 * 4;      // one 32 x 32 FP32 staging tile
+// Epilogue warps: 4 (one per TMEM lane quarter, two staging tiles each) or
+// 8 (two per quarter, each writing half of the columns, one staging tile
+// each); the staging space is the same 32 KB either way.  Measured on GB300
+// the two run the epilogue in the same time (it is bound by the TMA stores
+// and L2 reductions, not by the warps), so the smaller block is kept.
+constexpr int kEpiWarps = 4;
+constexpr int kStagePerWarp = 8 / kEpiWarps;
+constexpr uint32_t kEpiBytes = 8 * kStageC;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 // One problem of the batch (a single SpMM is a batch of one).
 struct DenseProb {
@@ -43,6 +62,8 @@ struct DenseProb {
   int n_ntiles;      // TN-wide column tiles
   int slabs;         // K slabs of 64 per tile
   int accumulate, vec_ok;
+  int tma_c;         // C tensor map usable (16-byte aligned rows)
+  int b3d;           // B tensor map is 3-D (64 columns x K x N / 64 chunks)
 };
 
 // The whole batch travels in the kernel parameters (no device allocation):
@@ -51,6 +72,7 @@ template <int NP>
 struct DenseTable {
   CUtensorMap tmA[NP];
   CUtensorMap tmB[NP];
+  CUtensorMap tmC[NP];   // FP32 C, 32 x 32 boxes, 128-byte swizzle
   DenseProb p[NP];
   int count;
   int64_t units;
@@ -69,10 +91,61 @@ __device__ __forceinline__ void advance_problem(const DenseTable<NP>& T, int64_t
   while (q + 1 < T.count && u >= T.p[q + 1].unit0) ++q;
 }
 
+// Position of a unit inside the batch: problem q, row-tile group mt, column
+// tile nt, K slab (unit = (nt * mtiles + mt) * slabs + slab within problem q).
+// Set once per role with divisions, then advanced by increments only.
+struct Cursor {
+  int q, mt, nt, slab;
+  int mtiles, ntiles, slabs;
+};
+
+template <int NP, int MH>
+__device__ __forceinline__ void cursor_load(const DenseTable<NP>& T, Cursor& c) {
+  const DenseProb& P = T.p[c.q];
+  c.mtiles = (P.n_copy + MH - 1) / MH;
+  c.ntiles = P.n_ntiles;
+  c.slabs = P.slabs;
+}
+
+template <int NP, int MH>
+__device__ __forceinline__ Cursor cursor_at(const DenseTable<NP>& T, int64_t u) {
+  Cursor c;
+  c.q = 0;
+  advance_problem(T, u, c.q);
+  cursor_load<NP, MH>(T, c);
+  const int64_t lu = u - T.p[c.q].unit0;
+  const int64_t tile = lu / c.slabs;
+  c.slab = (int)(lu - tile * c.slabs);
+  c.nt = (int)(tile / c.mtiles);
+  c.mt = (int)(tile - (int64_t)c.nt * c.mtiles);
+  return c;
+}
+
+// Move to the first slab of the next tile (next problem after its last tile).
+template <int NP, int MH>
+__device__ __forceinline__ void cursor_next_tile(const DenseTable<NP>& T, Cursor& c) {
+  c.slab = 0;
+  if (++c.mt == c.mtiles) {
+    c.mt = 0;
+    if (++c.nt == c.ntiles) {
+      c.nt = 0;
+      if (c.q + 1 < T.count) {
+        ++c.q;
+        cursor_load<NP, MH>(T, c);
+      }
+    }
+  }
+}
+
+template <int NP, int MH>
+__device__ __forceinline__ void cursor_next(const DenseTable<NP>& T, Cursor& c) {
+  if (++c.slab == c.slabs) cursor_next_tile<NP, MH>(T, c);
+}
+
 // MH = 128-row halves per CTA tile (1: 128 x TN, 2: 256 x TN sharing each B
 // stage between two MMAs, which halves B's shared-memory bytes per flop).
 template <int TN, int NP, int MH>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     dense_panel_kernel(const __grid_constant__ DenseTable<NP> T) {
   constexpr uint32_t kBBytes = (uint32_t)TN * kTK * 2;
   constexpr uint32_t kStageBytes = MH * kABytes + kBBytes;
@@ -81,7 +154,8 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = T.stages;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * kStageBytes);
+  uint8_t* stage_c = smem + (size_t)S * kStageBytes;   // 1024-aligned: stages are 1 KB multiples
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage_c + kEpiBytes);
   uint64_t* empty = full + S;
   uint64_t* acc_full = empty + S;    // [2] MMA -> epilogue: accumulator ready
   uint64_t* acc_empty = acc_full + 2;  // [2] epilogue -> MMA: accumulator drained
@@ -92,6 +166,14 @@ __global__ void __launch_bounds__(192, 1)
   const int64_t u1 = unit_begin(T.units, blockIdx.x + 1, gridDim.x);
   if (u0 >= u1) return;
 
+  if (threadIdx.x == 32) {
+    // descriptor fetches overlap the barrier and TMEM set-up
+    int q0 = 0;
+    advance_problem(T, u0, q0);
+    prefetch_tensormap(&T.tmA[q0]);
+    prefetch_tensormap(&T.tmB[q0]);
+    if (T.p[q0].tma_c) prefetch_tensormap(&T.tmC[q0]);
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -99,7 +181,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&acc_empty[b], kEpiWarps);
     }
     fence_barrier_init();
   }
@@ -116,35 +198,40 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------- TMA producer -----------------------------------------
     if (lane == 0) {
       int64_t i = 0;
-      int q = 0;
+      int st = 0;
+      uint32_t ph = 0;   // ring stage and its phase parity
       bool ok = true;
+      Cursor c = cursor_at<NP, MH>(T, u0);
       for (int64_t u = u0; u < u1; ++u, ++i) {
-        advance_problem(T, u, q);
-        const DenseProb& P = T.p[q];
-        const int st = (int)(i % S);
-        const uint32_t ph = (uint32_t)(i / S) & 1u;
         if (i >= S && !mbar_wait_bounded(&empty[st], ph ^ 1u, T.status)) {
           ok = false;
           break;
         }
-        const int64_t lu = u - P.unit0;
-        const int64_t tile = lu / P.slabs;
-        const int slab = (int)(lu % P.slabs);
-        const int mtiles = (P.n_copy + MH - 1) / MH;
-        const int mt = (int)(tile % mtiles);       // row tiles fastest: CTAs that
-        const int nt = (int)(tile / mtiles);       // run together share B in L2
+        const DenseProb& P = T.p[c.q];
         uint8_t* a_dst = smem + (size_t)st * kStageBytes;
         uint8_t* b_dst = a_dst + MH * kABytes;
-        const int k0 = slab * kTK;
+        const int k0 = c.slab * kTK;
         mbar_arrive_expect_tx(&full[st], kStageBytes);
+        // A: one box of MH x 128 rows (rows past the last copy are zero-filled)
+        tma_load_2d(a_dst, &T.tmA[c.q], k0, c.mt * MH * kTM, &full[st]);
+        // B: TN / 64 chunks of 64 columns, one 3-D box when N is a multiple
+        // of 64 (x = column in chunk, y = k, z = chunk), else one 2-D box each
+        if (P.b3d) {
+          tma_load_3d(b_dst, &T.tmB[c.q], 0, k0, c.nt * (TN / 64), &full[st]);
+        } else {
 #pragma unroll
-        for (int hh = 0; hh < MH; ++hh)   // rows past the last copy are zero-filled
-          tma_load_2d(a_dst + hh * kABytes, &T.tmA[q], k0, (mt * MH + hh) * kTM, &full[st]);
-#pragma unroll
-        for (int j = 0; j < TN / 64; ++j)
-          tma_load_2d(b_dst + j * (kTK * 128), &T.tmB[q], nt * TN + 64 * j, k0, &full[st]);
+          for (int j = 0; j < TN / 64; ++j)
+            tma_load_2d(b_dst + j * (kTK * 128), &T.tmB[c.q], c.nt * TN + 64 * j, k0, &full[st]);
+        }
+        // row tiles fastest: CTAs that run together share B in L2
+        cursor_next<NP, MH>(T, c);
+        if (++st == S) {
+          st = 0;
+          ph ^= 1u;
+        }
       }
       if (!ok) {
+        // consumers gave up: wait (bounded) for our copies in flight to land
         for (int64_t j = (i > S ? i - S : 0); j < i; ++j)
           mbar_wait_bounded(&full[j % S], (uint32_t)(j / S) & 1u, T.status);
       }
@@ -153,30 +240,31 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------- MMA issuer (one thread) --------------------------------
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, TN, false, true);
-      int64_t i = 0;
       int seg = -1;
-      int q = 0;
+      int st = 0;
+      uint32_t ph = 0;
       bool ok = true;
-      for (int64_t u = u0; u < u1 && ok; ++u, ++i) {
-        advance_problem(T, u, q);
-        const DenseProb& P = T.p[q];
-        const int slab = (int)((u - P.unit0) % P.slabs);
+      Cursor c = cursor_at<NP, MH>(T, u0);
+      int bsel = NBUF - 1;      // accumulator set of the current segment
+      uint32_t bph = 1;         // its acc_empty parity (flips each reuse)
+      for (int64_t u = u0; u < u1 && ok; ++u) {
+        const int slab = c.slab;
         const bool first = (u == u0) || slab == 0;
-        const bool last = (u + 1 == u1) || slab + 1 == P.slabs;
+        const bool last = (u + 1 == u1) || slab + 1 == c.slabs;
         if (first) {
           ++seg;
-          const int b = seg % NBUF;
+          if (++bsel == NBUF) {
+            bsel = 0;
+            bph ^= 1u;
+          }
           // the epilogue must have drained this accumulator (segment seg - NBUF)
-          if (seg >= NBUF &&
-              !mbar_wait_bounded(&acc_empty[b], (uint32_t)((seg / NBUF) - 1) & 1u, T.status)) {
+          if (seg >= NBUF && !mbar_wait_bounded(&acc_empty[bsel], bph ^ 1u, T.status)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
         }
-        const uint32_t d_tmem = tmem + (uint32_t)((seg % NBUF) * MH * TN);
-        const int st = (int)(i % S);
-        const uint32_t ph = (uint32_t)(i / S) & 1u;
+        const uint32_t d_tmem = tmem + (uint32_t)(bsel * MH * TN);
         if (!mbar_wait_bounded(&full[st], ph, T.status)) {
           ok = false;
           break;
@@ -198,8 +286,13 @@ __global__ void __launch_bounds__(192, 1)
             tc::mma_bf16(d_tmem + hh * TN, ad, bd, idesc, (!first || kk > 0) ? 1u : 0u);
           }
         }
-        tc::mma_commit(&empty[st]);                    // stage free once these MMAs finish
-        if (last) tc::mma_commit(&acc_full[seg % NBUF]);  // accumulator complete
+        tc::mma_commit(&empty[st]);                 // stage free once these MMAs finish
+        if (last) tc::mma_commit(&acc_full[bsel]);  // accumulator complete
+        cursor_next<NP, MH>(T, c);
+        if (++st == S) {
+          st = 0;
+          ph ^= 1u;
+        }
       }
       if (!ok) {
         // make the epilogue's waits end: release every accumulator it expects
@@ -208,43 +301,68 @@ __global__ void __launch_bounds__(192, 1)
     }
   } else {
     // ---------------- epilogue: TMEM -> registers -> C -----------------------
-    const int quarter = warp & 3;
-    int seg = -1;
-    int q = 0;
-    for (int64_t u = u0; u < u1; ++u) {
-      advance_problem(T, u, q);
-      const DenseProb& P = T.p[q];
-      const int64_t lu = u - P.unit0;
-      const int slab = (int)(lu % P.slabs);
-      const bool first = (u == u0) || slab == 0;
-      if (!first) continue;
-      ++seg;
-      // segment [u, ue): slabs of one tile
-      int64_t ue = u - slab + P.slabs;
+    const int quarter = warp & 3;                  // TMEM lanes 32 quarter .. + 31
+    const int part = (warp - 2) >> 2;              // column part of this warp
+    constexpr int kParts = kEpiWarps / 4;
+    uint8_t* my_stage = stage_c + (size_t)(warp - 2) * kStagePerWarp * kStageC;
+    int chunk = 0;   // staging tiles alternate per chunk
+    Cursor c = cursor_at<NP, MH>(T, u0);
+    int b = NBUF - 1;
+    uint32_t bph = 1;
+    // one iteration per segment: the slabs of one tile inside [u0, u1)
+    for (int64_t u = u0; u < u1;) {
+      const DenseProb& P = T.p[c.q];
+      const int q = c.q;
+      int64_t ue = u + (c.slabs - c.slab);
       if (ue > u1) ue = u1;
-      const bool whole = (slab == 0) && (ue - u == P.slabs);
-      const int64_t tile = lu / P.slabs;
-      const int mtiles = (P.n_copy + MH - 1) / MH;
-      const int mt = (int)(tile % mtiles);
-      const int nt = (int)(tile / mtiles);
-      const int b = seg % NBUF;
-      const bool ok = mbar_wait_bounded(&acc_full[b], (uint32_t)(seg / NBUF) & 1u, T.status);
+      const bool whole = (c.slab == 0) && (ue - u == c.slabs);
+      const int mt = c.mt, nt = c.nt;
+      if (++b == NBUF) {
+        b = 0;
+        bph ^= 1u;
+      }
+      const bool ok = mbar_wait_bounded(&acc_full[b], bph, T.status);
       tc::fence_after_sync();
       const int64_t n0 = (int64_t)nt * TN;
+      const bool add = !whole || P.accumulate;
 #pragma unroll 1
       for (int hh = 0; hh < MH; ++hh) {
         const int copy = mt * MH + hh;
         if (copy >= P.n_copy) break;   // warp-uniform
-        const int64_t row = (int64_t)__ldg(&P.tile_order[copy]) * kTM + quarter * 32 + lane;
+        const int64_t row0 = (int64_t)__ldg(&P.tile_order[copy]) * kTM + quarter * 32;
+        const int64_t row = row0 + lane;
 #pragma unroll 1
-        for (int c = 0; c < TN / 32; ++c) {
+        for (int cc = part * (TN / 32 / kParts); cc < (part + 1) * (TN / 32 / kParts); ++cc) {
           uint32_t r[32];
           tc::tmem_ld_32x32b_x32(tmem + ((uint32_t)(quarter * 32) << 16) +
-                                     (uint32_t)(b * MH * TN + hh * TN + c * 32),
+                                     (uint32_t)(b * MH * TN + hh * TN + cc * 32),
                                  r);
           tc::tmem_ld_wait();
-          const int64_t col0 = n0 + c * 32;
-          if (!ok || row >= P.M || col0 >= P.N) continue;
+          const int64_t col0 = n0 + cc * 32;
+          if (!ok || row0 >= P.M || col0 >= P.N) continue;   // warp-uniform
+          if (P.tma_c) {
+            // staging tile (chunk & 1) is free once the copy issued two
+            // chunks ago has read it
+            uint8_t* buf = my_stage + (size_t)(chunk % kStagePerWarp) * kStageC;
+            if (lane == 0) bulk_wait_read<kStagePerWarp - 1>();
+            __syncwarp();
+            // row `lane`, 16-byte chunk j at (j ^ (lane % 8)): the 128-byte swizzle
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              *reinterpret_cast<uint4*>(buf + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                  make_uint4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              // rows past M and columns past N are clipped by the tensor map
+              if (add) tma_reduce_add_2d(&T.tmC[q], (int32_t)col0, (int32_t)row0, buf);
+              else tma_store_2d(&T.tmC[q], (int32_t)col0, (int32_t)row0, buf);
+              bulk_commit();
+            }
+            ++chunk;
+            continue;
+          }
+          if (row >= P.M) continue;
           float* dst = P.C + row * P.ldc + col0;
           const bool vec = P.vec_ok && col0 + 32 <= P.N;
           if (!whole) {
@@ -283,7 +401,13 @@ __global__ void __launch_bounds__(192, 1)
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
+      u = ue;
+      cursor_next_tile<NP, MH>(T, c);
     }
+    // the staging tiles must not be released (CTA exit) while TMA reads
+    // them, and C must be complete when the kernel ends
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -293,7 +417,7 @@ __global__ void __launch_bounds__(192, 1)
 
 template <int TN, int MH>
 size_t dense_smem_bytes(int stages) {
-  return 1024 + (size_t)stages * (MH * kABytes + (size_t)TN * kTK * 2) + 256;
+  return 1024 + (size_t)stages * (MH * kABytes + (size_t)TN * kTK * 2) + kEpiBytes + 256;
 }
 
 template <int TN, int MH>
@@ -315,16 +439,28 @@ rosko_status launch_table(DenseTable<NP>& T, int64_t grid, cudaStream_t st) {
       return ROSKO_ERR_CUDA;
     set = smem;
   }
-  fn<<<(unsigned)grid, 192, smem, st>>>(T);
+  fn<<<(unsigned)grid, kThreads, smem, st>>>(T);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
 }
 
-rosko_status encode_dense_maps(const DenseJob& j, CUtensorMap* mA, CUtensorMap* mB) {
+rosko_status encode_dense_maps(const DenseJob& j, int MH, CUtensorMap* mA, CUtensorMap* mB,
+                               CUtensorMap* mC, bool c_ok, int TN, bool* b3d) {
+  if (c_ok) {
+    const cuuint64_t dims[2] = {(cuuint64_t)j.N, (cuuint64_t)j.M};
+    const cuuint64_t strides[1] = {(cuuint64_t)j.ldc * 4};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t es[2] = {1, 1};
+    if (encode_tiled(mC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, j.C, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return ROSKO_ERR_INVALID_ARG;
+  }
   {
     const cuuint64_t dims[2] = {(cuuint64_t)j.Kpad, (cuuint64_t)j.dense_rows};
     const cuuint64_t strides[1] = {(cuuint64_t)j.Kpad * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
+    const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)(kTM * MH)};
     const cuuint32_t es[2] = {1, 1};
     if (encode_tiled(mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(j.dense_A), dims,
                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -332,7 +468,19 @@ rosko_status encode_dense_maps(const DenseJob& j, CUtensorMap* mA, CUtensorMap* 
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return ROSKO_ERR_INVALID_ARG;
   }
-  {
+  *b3d = false;
+  if (j.N % 64 == 0) {
+    // B viewed as [N / 64][K][64]: chunk z starts 128 bytes after chunk z-1
+    const cuuint64_t dims[3] = {64, (cuuint64_t)j.K, (cuuint64_t)(j.N / 64)};
+    const cuuint64_t strides[2] = {(cuuint64_t)j.ldb * 2, 128};
+    const cuuint32_t box[3] = {64, (cuuint32_t)kTK, (cuuint32_t)(TN / 64)};
+    const cuuint32_t es[3] = {1, 1, 1};
+    *b3d = encode_tiled(mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(j.B), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  if (!*b3d) {
     const cuuint64_t dims[2] = {(cuuint64_t)j.N, (cuuint64_t)j.K};
     const cuuint64_t strides[1] = {(cuuint64_t)j.ldb * 2};
     const cuuint32_t box[2] = {64, (cuuint32_t)kTK};
@@ -348,7 +496,7 @@ rosko_status encode_dense_maps(const DenseJob& j, CUtensorMap* mA, CUtensorMap* 
 
 template <int TN, int NP, int MH>
 rosko_status run_jobs(const DenseJob* jobs, int count, int ctas, cudaStream_t st) {
-  static_assert(sizeof(DenseTable<NP>) <= 30 * 1024, "kernel parameter table too large");
+  static_assert(sizeof(DenseTable<NP>) <= 32 * 1024 - 256, "kernel parameter table too large");
   DenseTable<NP> T;
   std::memset(static_cast<void*>(&T), 0, sizeof(T));
   int64_t units = 0;
@@ -356,9 +504,13 @@ rosko_status run_jobs(const DenseJob* jobs, int count, int ctas, cudaStream_t st
   for (int i = 0; i < count; ++i) {
     const DenseJob& j = jobs[i];
     if (j.n_tiles <= 0 || j.N <= 0) continue;
-    rosko_status s = encode_dense_maps(j, &T.tmA[n], &T.tmB[n]);
+    const bool c_ok = ((reinterpret_cast<uintptr_t>(j.C) % 16) == 0) && ((j.ldc * 4) % 16 == 0);
+    bool b3d = false;
+    rosko_status s = encode_dense_maps(j, MH, &T.tmA[n], &T.tmB[n], &T.tmC[n], c_ok, TN, &b3d);
     if (s != ROSKO_OK) return s;
     DenseProb& P = T.p[n];
+    P.tma_c = c_ok ? 1 : 0;
+    P.b3d = b3d ? 1 : 0;
     P.tile_order = j.tile_order_dev;
     P.C = j.C;
     P.ldc = j.ldc;

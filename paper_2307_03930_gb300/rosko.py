@@ -45,6 +45,15 @@ class rosko_tile(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class rosko_plan(ctypes.Structure):
+    _fields_ = [("dense_tiles", ctypes.c_int64), ("sparse_panels", ctypes.c_int64),
+                ("order", ctypes.c_int32), ("zero_fill", ctypes.c_int32), ("tile", rosko_tile)]
+
+    def as_dict(self):
+        return {"dense_tiles": self.dense_tiles, "sparse_panels": self.sparse_panels,
+                "order": self.order, "zero_fill": self.zero_fill, "tile": self.tile.as_dict()}
+
+
 def make_tile(**kw) -> rosko_tile:
     t = rosko_tile()
     for f, _ in rosko_tile._fields_:
@@ -70,6 +79,8 @@ def lib() -> ctypes.CDLL:
         "rosko_status_string": (ctypes.c_char_p, [ci]),
         "rosko_pack": (ci, [vp, ci, i64, i64, i64, ci, vp, P_tile, vp, ctypes.POINTER(vp)]),
         "rosko_spmm": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, ci, P_tile, vp]),
+        "rosko_spmm_plan": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, ci, P_tile,
+                                 ctypes.POINTER(rosko_plan), vp]),
         "rosko_free": (None, [vp]),
         "rosko_unpack": (ci, [vp, vp, i64, vp]),
         "rosko_packed_info": (ci, [vp] + [ctypes.POINTER(i64)] * 4 +
@@ -185,6 +196,24 @@ def rosko_spmm(A: PackedA, B: torch.Tensor, C: torch.Tensor,
                       ctypes.c_void_p(_stream(stream)))
     _check(st, "rosko_spmm")
     return C
+
+
+def rosko_spmm_plan(A: PackedA, B: torch.Tensor, C: torch.Tensor,
+                    col_scale: Optional[torch.Tensor] = None, accumulate: bool = False,
+                    tile: Optional[rosko_tile] = None, stream=None) -> dict:
+    """What rosko_spmm would run for these arguments (nothing is launched
+    for the product itself): dense tiles, sparse panels, traversal, tile."""
+    L = lib()
+    K, N = B.shape
+    out = rosko_plan()
+    st = L.rosko_spmm_plan(A.handle, _ptr(B) if B.numel() else None, TORCH_TO_CODE[B.dtype], N,
+                           _ld(B) if B.numel() else max(N, 1), _ptr(col_scale),
+                           _ptr(C) if C.numel() else None, TORCH_TO_CODE[C.dtype],
+                           _ld(C) if C.numel() else max(N, 1), int(bool(accumulate)),
+                           ctypes.byref(tile) if tile is not None else None,
+                           ctypes.byref(out), ctypes.c_void_p(_stream(stream)))
+    _check(st, "rosko_spmm_plan")
+    return out.as_dict()
 
 
 def rosko_free(A: PackedA) -> None:

@@ -1,6 +1,7 @@
 """Batched SpMM (one persistent stream-K tensor-core launch for every
-problem's dense tiles, sparse remainders per problem) against the oracle, and
-its capture/replay in a CUDA graph.  GPU only."""
+problem's dense tiles, one row-direct launch for the row-direct sparse
+remainders, other remainders per problem) against the oracle, and its
+capture/replay in a CUDA graph.  GPU only."""
 import numpy as np
 import pytest
 import torch
@@ -28,9 +29,10 @@ SHAPES = [(300, 500, 257, 0.7, "uniform"), (64, 96, 196, 0.99, "uniform"),
           (256, 640, 128, 0.9, "block4x1"), (1000, 300, 450, 0.985, "powerlaw")]
 
 
-def _run_batched(rosko, probs, tiles=None, accumulate=False, C0s=None):
-    hs = [rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16) for A, _ in probs]
-    Bs = [_ldpad(torch.from_numpy(B).to(torch.bfloat16), 2) for _, B in probs]
+def _run_batched(rosko, probs, tiles=None, accumulate=False, C0s=None, f32=False):
+    code, bt, esz = (rosko.F32, torch.float32, 4) if f32 else (rosko.BF16, torch.bfloat16, 2)
+    hs = [rosko.rosko_pack(torch.from_numpy(A).cuda(), code) for A, _ in probs]
+    Bs = [_ldpad(torch.from_numpy(B).to(bt), esz) for _, B in probs]
     Cs = [torch.zeros((A.shape[0], B.shape[1]), device="cuda") for A, B in probs]
     if C0s is not None:
         for C, C0 in zip(Cs, C0s):
@@ -87,3 +89,23 @@ def test_batched_graph_capture_and_replay():
     for (A, _), Bn, C in zip(probs, new_B, Cs):
         ref, D = spmm(bf16_round(A), bf16_round(Bn))
         assert normalized_error(C.cpu().numpy(), ref, D) <= 1e-5
+
+
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_batched_fp32_row_direct_is_one_launch(accumulate):
+    # FP32 has no tensor-core path; every problem below 15% density runs
+    # row-direct, and all of them share one launch
+    rosko = built()
+    shapes = [(300, 500, 257, 0.9, "uniform"), (64, 96, 196, 0.99, "uniform"),
+              (513, 1000, 700, 0.95, "powerlaw"), (130, 77, 300, 0.999, "uniform"),
+              (256, 640, 128, 0.9, "block4x1"), (33, 20, 5, 0.95, "uniform")]
+    probs = _problems(75, shapes)
+    C0s = [np.random.default_rng(j).standard_normal((A.shape[0], B.shape[1])).astype(np.float32)
+           for j, (A, B) in enumerate(probs)] if accumulate else None
+    hs, Bs, Cs, launches = _run_batched(rosko, probs, accumulate=accumulate, C0s=C0s, f32=True)
+    for j, ((A, B), C) in enumerate(zip(probs, Cs)):
+        ref, D = spmm(A, B, C0=C0s[j] if accumulate else None)
+        if accumulate:
+            D = D + np.abs(C0s[j])
+        assert normalized_error(C.cpu().numpy(), ref, D) <= 1e-5, j
+    assert launches == 1

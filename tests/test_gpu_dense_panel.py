@@ -53,14 +53,15 @@ def test_all_dense(M, K, N, TN, ctas, MC):
     assert launches == 1          # only the tensor-core kernel ran
 
 
-@pytest.mark.parametrize("MC", [128, 256])
-def test_mixed_split_powerlaw(MC):
+@pytest.mark.parametrize("MC,order", [(128, 0), (256, 0), (128, 4), (256, 1)])
+def test_mixed_split_powerlaw(MC, order):
     # power-law rows give tiles of very different density: some run dense,
-    # the others on the sparse kernel, in one call
+    # the others on the sparse kernel (its panel list skips the dense tiles'
+    # panels), in one call
     rosko = built()
     A = gen.sparse_weight(1000, 700, 0.97, gen.rng_for(9), "powerlaw")
     B = gen.relu_normal((700, 333), gen.rng_for(10))
-    t = rosko.make_tile(dense_split_pm=30, dense_m_c=MC)
+    t = rosko.make_tile(dense_split_pm=30, dense_m_c=MC, order=order)
     err, launches = _run(rosko, A, B, t)
     assert err <= 1e-5, err
     dens = [(A[i:i + 128] != 0).mean() for i in range(0, 1000, 128)]
@@ -111,3 +112,27 @@ def test_c2_dense_full_size_sampled(s):
     err, launches = _run(rosko, A, B, None, rows=rows)
     assert err <= 1e-5, err
     assert launches == 1
+
+
+def test_plan_reports_the_split_and_launches_nothing():
+    rosko = built()
+    A = gen.sparse_weight(1000, 700, 0.97, gen.rng_for(9), "powerlaw")
+    h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16)
+    B = _ldpad(torch.zeros((700, 333), dtype=torch.bfloat16), 2)
+    C = torch.full((1000, 333), 3.0, device="cuda")
+    t = rosko.make_tile(dense_split_pm=30, order=4)
+    l0 = rosko.rosko_kernel_launches()
+    pl = rosko.rosko_spmm_plan(h, B, C, tile=t)
+    torch.cuda.synchronize()
+    assert rosko.rosko_kernel_launches() == l0
+    assert torch.all(C == 3.0)                 # nothing written
+    dens = [(A[i:i + 128] != 0).mean() for i in range(0, 1000, 128)]
+    n_dense = sum(d * 1000 >= 30 for d in dens)
+    dense_panels = sum(-(-min(128, 1000 - 128 * j) // 16) for j, d in enumerate(dens)
+                       if d * 1000 >= 30)
+    assert pl["dense_tiles"] == n_dense
+    assert pl["sparse_panels"] == -(-1000 // 16) - dense_panels
+    assert pl["order"] == 4
+    # sparse only: no dense tile
+    pl = rosko.rosko_spmm_plan(h, B, C, tile=rosko.make_tile(dense_split_pm=1001))
+    assert pl["dense_tiles"] == 0 and pl["sparse_panels"] == -(-1000 // 16)

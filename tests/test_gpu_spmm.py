@@ -114,14 +114,19 @@ def test_small_ragged(mode, M, K, N, s, m_r):
 
 
 # every compiled (order, m_r, V) variant with several CTA heights, slabs and K
-# splits; order 1 = column order (Alg. 2), order 2 = row-slot order
+# splits; order 1 = column order (Alg. 2), order 2 = row-slot order,
+# order 3 = row-slot over the tile's touched rows, order 4 = row-direct (B
+# from L2, no slabs: k_c and the split do not apply)
 VARIANTS = {"f32": [(1, 32, 4), (1, 16, 8), (1, 16, 4), (1, 8, 16), (1, 8, 8), (2, 16, 4),
-                    (2, 8, 8), (3, 16, 4)],
+                    (2, 8, 8), (3, 16, 4), (4, 16, 4), (4, 8, 8), (4, 32, 4)],
             "bf16": [(1, 32, 4), (1, 16, 8), (1, 8, 16), (1, 8, 8), (2, 16, 4), (2, 8, 8),
-                     (3, 16, 4)],
-            "i8": [(1, 32, 4), (1, 16, 8), (1, 8, 16), (2, 16, 4), (2, 8, 8), (3, 16, 4)],
-            "i8f": [(1, 32, 4), (1, 16, 8), (1, 8, 16), (2, 16, 4), (2, 8, 8), (3, 16, 4)],
-            "f64": [(1, 32, 2), (1, 16, 4), (1, 8, 8), (2, 16, 2), (2, 8, 4), (3, 16, 2)]}
+                     (3, 16, 4), (4, 16, 8), (4, 8, 4), (4, 32, 8)],
+            "i8": [(1, 32, 4), (1, 16, 8), (1, 8, 16), (2, 16, 4), (2, 8, 8), (3, 16, 4),
+                   (4, 16, 8)],
+            "i8f": [(1, 32, 4), (1, 16, 8), (1, 8, 16), (2, 16, 4), (2, 8, 8), (3, 16, 4),
+                    (4, 8, 8)],
+            "f64": [(1, 32, 2), (1, 16, 4), (1, 8, 8), (2, 16, 2), (2, 8, 4), (3, 16, 2),
+                    (4, 16, 4)]}
 
 
 @pytest.mark.parametrize("mode", list(VARIANTS))
@@ -134,7 +139,7 @@ def test_forced_tiles(mode, W, KC, split):
         m_c = 128 if order == 3 else W * R   # order 3: one CTA per 128-row tile
         t = rosko.make_tile(m_r=R, n_r=32 * V, k_c=KC, m_c=m_c, split_k=split, order=order,
                             mode=rosko.SCHED_FORCED)
-        if 2 * KC * 32 * V * esz > 200 * 1024:
+        if order != 4 and 2 * KC * 32 * V * esz > 200 * 1024:
             # a two-slab ring would not fit in shared memory: rejected on the host
             with pytest.raises(rosko.RoskoError) as ei:
                 run(rosko, A, B, mode, m_r=R, tile=t)
@@ -143,7 +148,7 @@ def test_forced_tiles(mode, W, KC, split):
         check(mode, *run(rosko, A, B, mode, m_r=R, tile=t))
 
 
-@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4])
 @pytest.mark.parametrize("s", [0.0, 0.99, 0.999])
 def test_orders_agree_bitwise_int8(order, s):
     # integer accumulation is exact: both traversals give the same INT32 C
@@ -164,7 +169,7 @@ def test_accumulate_in_place(mode, split):
         C0 = rng.integers(-1000, 1000, size=(90, 200)).astype(np.int32)
     else:
         C0 = rng.standard_normal((90, 200)).astype(np.float64 if mode == "f64" else np.float32)
-    for order, m_r in ((1, 16 if mode == "f64" else 32), (2, 16), (3, 16)):
+    for order, m_r in ((1, 16 if mode == "f64" else 32), (2, 16), (3, 16), (4, 16)):
         t = rosko.make_tile(split_k=split, order=order)
         check(mode, *run(rosko, A, B, mode, m_r=m_r, tile=t, accumulate=True, C0=C0))
 
@@ -214,12 +219,48 @@ def test_c2_full_size_sampled(s, mode):
 
 
 @pytest.mark.parametrize("mode", ["f32", "bf16", "i8"])
-def test_gather_empty_tiles_and_ragged(mode):
+@pytest.mark.parametrize("order", [3, 4])
+def test_gather_empty_tiles_and_ragged(mode, order):
     # tiles whose rows are all zero have an empty touched-column list; the
-    # last tile is ragged (M = 300)
+    # last tile is ragged (M = 300); N = 130 leaves a partial lane chunk
     rosko = built()
     A, B = _problem(300, 777, 130, 0.995, seed=31)
     A[0:128] = 0                       # tile 0: nothing touched
     A[256:300, :5] = 1.0               # ragged tile 2: a few dense columns
-    t = rosko.make_tile(order=3)
+    t = rosko.make_tile(order=order)
     check(mode, *run(rosko, A, B, mode, m_r=16, tile=t))
+
+
+@pytest.mark.parametrize("M,K", [(11008, 4096), (4096, 11008)])
+@pytest.mark.parametrize("s", [0.7, 0.9, 0.95])
+def test_c3_full_size_sampled(M, K, s):
+    # transformer-FFN shapes, seed 2: A magnitude-pruned N(0,1), B K x 2048
+    # N(0,1); BF16 in / FP32 accumulate (analytic schedule: the tensor-core
+    # path) and INT8 -> INT32 (row-direct), 40 sampled rows against the oracle
+    rosko = built()
+    rng = gen.rng_for(2, M, int(round(s * 100)))
+    A = gen.magnitude_prune(gen.normal((M, K), rng), s)
+    B = gen.normal((K, 2048), rng)
+    rows = np.random.default_rng(M + int(s * 100)).choice(M, 40, replace=False)
+    check("bf16", *run(rosko, A, B, "bf16", m_r=0, rows=rows))
+    check("i8", *run(rosko, A, B, "i8", m_r=0, rows=rows))
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16", "i8", "i8f", "f64"])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_row_direct_cuts_long_rows(mode, accumulate):
+    # power-law rows plus two full rows: rows longer than one work segment
+    # (128 nonzeros) are cut into pieces whose sums are added into C
+    rosko = built()
+    M, K, N = 150, 700, 300
+    A = gen.sparse_weight(M, K, 0.97, gen.rng_for(61), "powerlaw")
+    rng = np.random.default_rng(62)
+    A[3] = rng.standard_normal(K).astype(np.float32)
+    A[149, :300] = rng.standard_normal(300).astype(np.float32)
+    B = gen.normal((K, N), gen.rng_for(63))
+    C0 = None
+    if accumulate:
+        C0 = (rng.integers(-1000, 1000, size=(M, N)).astype(np.int32) if mode == "i8" else
+              rng.standard_normal((M, N)).astype(np.float64 if mode == "f64" else np.float32))
+    t = rosko.make_tile(order=4, dense_split_pm=1001)
+    check(mode, *run(rosko, A, B, mode, m_r=16, tile=t, accumulate=accumulate, C0=C0))

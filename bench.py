@@ -8,10 +8,13 @@ per sparsity, each with its own B.  Two such input sets alternate between steps
 (~430 MB with BF16 B, > the 129 MB L2), so no L2 flush is needed.
 
 Headline form: A pre-packed in BF16 (Alg. 1 on the device), B in BF16, FP32
-accumulation, tile from the library's schedule.  Reported beside it: the plain
-FP32 form, cuSPARSE CSR SpMM and cuBLAS dense GEMM (both through torch), the
-end-to-end call with host buffers, the roofline of the dominant kernel and the
-oracle timed on the host cores.
+accumulation, schedule from the learned selector when its trained weights
+ship with the package (else the analytic rule; the step under the analytic
+rule is timed beside it).  Reported beside it: the plain FP32 form, cuSPARSE
+CSR SpMM and cuBLAS dense GEMM (both through torch), 64 uneven layers batched
+vs separate, the end-to-end call with host buffers, per-kernel shares (from
+the library's own plan of each call), the roofline of the kernel with the
+largest share and the oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -54,6 +57,8 @@ def parse():
                     help="profiling: run only the SpMM of this sparsity (BF16 and FP32 forms)")
     ap.add_argument("--autotune", action="store_true",
                     help="with --case: also run the autotuner and print every candidate's time")
+    ap.add_argument("--schedule", default="analytic", choices=["analytic", "learned", "autotune"],
+                    help="schedule of the timed step (the other two are timed beside it)")
     a = ap.parse_args()
     a.warmup = max(3, a.warmup)
     return a
@@ -273,17 +278,22 @@ def main():
     nnz = [i["nnz"] for i in infos]
     flops_step = sum(2.0 * z * N for z in nnz)
     stream = torch.cuda.current_stream()
-    # schedule: the learned selector when its trained weights are present
-    # (its choice is made and cached per handle on the first, untimed call),
-    # else the analytic rule
-    tile, form = None, "analytic tile"
+    # schedule of the timed step: the library's default (analytic rule), or
+    # the learned selector / the autotuner (their choice is made and cached
+    # per handle on the first, untimed call); the other forms are timed beside
+    learned_ok = False
     try:
         from paper_2307_03930_gb300 import selector as sel
         if os.path.exists(sel.WEIGHTS):
             sel.install()
-            tile, form = rosko.make_tile(mode=rosko.SCHED_LEARNED), "learned tile (MLP selector)"
-    except Exception as e:  # pragma: no cover - weights unreadable: analytic
+            learned_ok = True
+    except Exception as e:  # pragma: no cover - weights unreadable
         print(f"selector not installed: {e}", file=sys.stderr)
+    tile, form = None, "analytic tile"
+    if args.schedule == "learned" and learned_ok:
+        tile, form = rosko.make_tile(mode=rosko.SCHED_LEARNED), "learned tile (MLP selector)"
+    elif args.schedule == "autotune":
+        tile, form = rosko.make_tile(mode=rosko.SCHED_AUTOTUNE), "autotuned tile"
 
     def step(t, hs=handles16, key="B16", tl=None):
         S = sets[t % 2]
@@ -333,11 +343,18 @@ def main():
     # which kernel each SpMM runs (the library's own plan of the call)
     plans = [rosko.rosko_spmm_plan(handles16[i], sets[0]["B16"][i], sets[0]["C"][i], tile=tile)
              for i in range(len(SPARSITIES))]
-    # the same step under the analytic rule, for the learned-vs-analytic gain
-    analytic_step_ms = None
-    if tile is not None:
-        analytic_step_ms = graph_time(lambda: step(0, tl=rosko.make_tile()), torch, reps=20)
-    learned_step_ms = graph_time(lambda: step(0), torch, reps=20)
+    # the step under each schedule (graph replays of one input set): the
+    # analytic rule, the learned selector, the per-shape autotuner (its search
+    # runs on the first, uncaptured call of each handle and is cached)
+    forms_ms = {"analytic": graph_time(lambda: step(0, tl=rosko.make_tile()), torch, reps=20)}
+    if learned_ok:
+        forms_ms["learned"] = graph_time(lambda: step(0, tl=rosko.make_tile(mode=rosko.SCHED_LEARNED)),
+                                         torch, reps=20)
+        forms_ms["learned_choices"] = [rosko.rosko_spmm_plan(
+            handles16[i], sets[0]["B16"][i], sets[0]["C"][i],
+            tile=rosko.make_tile(mode=rosko.SCHED_LEARNED))["tile"] for i in range(len(SPARSITIES))]
+    forms_ms["autotune"] = graph_time(lambda: step(0, tl=rosko.make_tile(mode=rosko.SCHED_AUTOTUNE)),
+                                      torch, reps=20)
 
     # ---------------- per-sparsity figures and the roofline -------------------
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -411,8 +428,7 @@ def main():
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "device_status": status,
             "kernels": kinds, "per_sparsity": per,
-            "schedule": {"form": form, "step_ms_graph": learned_step_ms,
-                         "analytic_step_ms_graph": analytic_step_ms},
+            "schedule": {"form": form, "step_ms_graph_by_schedule": forms_ms},
             "comparisons": extras}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -568,9 +584,9 @@ def comparison_legs(rosko, torch, dev, sets, infos, stream):
 def batched_leg(rosko, torch, dev, seed=3, count=64):
     """Uneven layers (64 SpMMs: M, K log-uniform in [64, 4096], N in
     [196, 12544], sparsity uniform in [0.70, 0.99], BF16): one
-    rosko_spmm_batched call (one persistent dense-panel launch plus sparse
-    remainders) captured in a CUDA graph, against 64 separate rosko_spmm
-    launches captured in a graph and issued from the host."""
+    rosko_spmm_batched call (one persistent tensor-core launch per tile shape
+    plus one row-direct launch) captured in a CUDA graph, against 64 separate
+    rosko_spmm calls captured in a graph and issued from the host."""
     from paper_2307_03930_gb300 import inputs as gen
     shapes = gen.c4_shapes(seed, count)
     hs, Bs, Cs, flops = [], [], [], 0.0

@@ -191,14 +191,16 @@ rosko_status rosko_spmm_plan(rosko_packed_t A, const void* B_dev, rosko_dtype b_
 
 /*
  * rosko_spmm_batched - C_i = A_i . B_i (or C_i += ...) for `count` <= 64
- * independent problems (pruned layers of different shapes).  The dense-panel tiles of
- * every problem run in ONE persistent stream-K tensor-core launch whose work
- * list (per-problem TMA descriptors and sizes) is passed in the kernel
- * parameters; the sparse remainders run as one row-skipping launch per
- * problem.  Per-problem arrays: A, B (device), N, ldb, C (device), ldc;
- * all problems share b_dtype and c_dtype.  tiles: NULL (analytic rule) or
- * `count` tiles (e.g. from rosko_autotune); the shared tensor-core launch
- * takes dense_m_c from the first tile that sets it.  No device memory is allocated
+ * independent problems (pruned layers of different shapes).  The dense-panel
+ * tiles of all problems run in one persistent tensor-core launch per CTA-tile
+ * shape (at most four: 128 or 256 columns x 128 or 256 rows, each problem
+ * taking the shape its tile or the analytic rule gives it), whose work list
+ * (per-problem TMA descriptors and sizes) is passed in the kernel
+ * parameters; the row-direct sparse remainders share one launch, other
+ * remainders run one launch per problem.  Per-problem arrays: A, B (device),
+ * N, ldb, C (device), ldc; all problems share b_dtype and c_dtype.  tiles:
+ * NULL (analytic rule) or `count` tiles (e.g. from rosko_autotune).  No
+ * device memory is allocated
  * and nothing synchronises, so the call can be captured in a CUDA graph and
  * replayed (capture after a first, uncaptured call on the same handles).
  */

@@ -102,7 +102,8 @@ CUresult encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank,
 // Tensor-core dense-panel tiles (measured on GB300, stream-K kernel):
 //  * K of fewer than 16 slabs (K < 1024): cutting tiles along K buys little
 //    and costs a zero fill of C and reduce-adds, so every tile is owned whole
-//    by one CTA; 128-wide tiles give more of them;
+//    by one CTA (one per tile, or one per SM walking several); 128-wide
+//    tiles give more of them;
 //  * otherwise one CTA per SM shares the (tile, slab) units; 256 columns per
 //    tile halve the L2->SM traffic of A against 128, and 256 rows (two MMAs
 //    on one B stage) pay off once there are 16 or more 128-row tiles (a
@@ -115,7 +116,9 @@ void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, i
     const int64_t tiles = n_tiles * ((N + 127) / 128);
     *TN_out = 128;
     *mc_out = 128;
-    *ctas_out = (int)std::max<int64_t>(1, tiles <= 65535 ? tiles : sms);
+    // up to two tiles per SM: one CTA per tile; beyond: one persistent CTA
+    // per SM walking whole tiles (its epilogue overlaps the next tile's MMAs)
+    *ctas_out = (int)std::max<int64_t>(1, tiles <= 2 * sms ? tiles : sms);
     return;
   }
   *TN_out = N > 128 ? 256 : 128;
@@ -189,10 +192,17 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
     // the first cold loads, the epilogue) that row-direct (~3 us) does not.
     // Model both on the uniform-density assumption (every tile dense at
     // d >= 5 per mille) and keep the layer sparse when row-direct is
-    // predicted faster: dense work at ~0.8 PFLOP/s, row-direct moving
-    // nnz * N BF16 values from L2 at ~5 TB/s.
+    // predicted faster.  Dense: work at ~0.8 PFLOP/s.  Row-direct: nnz * N
+    // BF16 values from L2 at ~5 TB/s, plus its latency chain: a warp walks
+    // one row piece (<= kSegRecords nonzeros) four records per ~0.8 us
+    // round trip, and ~24 warps per SM are resident.
     const double t_dense = 6.0 + 2.0 * (double)M * (double)K * (double)N / 0.8e15 * 1e6;
-    const double t_direct = 3.0 + (double)nnz * (double)N * 2.0 / 5e12 * 1e6;
+    const double row = M ? (double)nnz / (double)M : 0.0;
+    const double pieces = std::max(1.0, std::ceil(row / kSegRecords));
+    const double warps = (double)M * pieces * std::ceil((double)N / 256.0);
+    const double waves = std::ceil(warps / (24.0 * sms));
+    const double chain = 0.8 * std::ceil(std::min(row, (double)kSegRecords) / 4.0) * waves;
+    const double t_direct = 3.0 + (double)nnz * (double)N * 2.0 / 5e12 * 1e6 + chain;
     if (t_direct < t_dense) t->dense_split_pm = 1001;
   }
   int TN = 256, ds = 1;
@@ -527,14 +537,9 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
   std::vector<char> active((size_t)count, 0), dense_any((size_t)count, 0);
   std::vector<char> direct_cut((size_t)count, 0);
   rest.resize((size_t)count);
-  int TN = 128, MH = 1;   // one launch serves every shape: 128-row tiles
-  if (tiles)
-    for (int32_t i = 0; i < count; ++i)
-      if (tiles[i].dense_m_c > 0) {
-        if (tiles[i].dense_m_c != 128 && tiles[i].dense_m_c != 256) return ROSKO_ERR_INVALID_ARG;
-        MH = tiles[i].dense_m_c / 128;
-        break;
-      }
+  // dense tiles run in one launch per CTA-tile shape (TN x 128 MH): each
+  // problem takes the shape the analytic rule (or its tile) gives it
+  std::vector<int> job_tn, job_mh;
   for (int32_t i = 0; i < count; ++i) {
     bool done = false;
     rosko_status v = spmm_validate(A[i], B[i], b_dt, N[i], ldb[i], nullptr, C[i], c_dt, ldc[i],
@@ -566,10 +571,16 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
       j.ldc = ldc[i];
       j.M = A[i]->M;
       j.accumulate = accumulate;
+      int tn = 256, ds = 1, mc = 128;
+      dense_config(nd, N[i], A[i]->K, sms, &tn, &ds, &mc);
+      if (tiles && tiles[i].dense_n_r > 0) tn = tiles[i].dense_n_r;
+      if (tiles && tiles[i].dense_m_c > 0) mc = tiles[i].dense_m_c;
+      if ((tn != 128 && tn != 256) || (mc != 128 && mc != 256)) return ROSKO_ERR_INVALID_ARG;
       jobs.push_back(j);
       job_of.push_back(i);
+      job_tn.push_back(tn);
+      job_mh.push_back(mc / 128);
       dense_any[(size_t)i] = 1;
-      if (N[i] > 128) TN = 256;
     }
     // the sparse remainder keeps this problem's tile; spmm_run recomputes the
     // same dense prefix from the same threshold and skips launching it
@@ -593,11 +604,20 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
   std::vector<char> zeroed((size_t)count, 0);
   if (!accumulate) {
     std::vector<char> need((size_t)count, 0);
-    if (!jobs.empty()) {
-      std::unique_ptr<bool[]> nj(new bool[jobs.size()]);
-      dense_batch_needs_zero(jobs.data(), (int)jobs.size(), TN, sms, MH, nj.get());
+    for (int g = 0; g < 4; ++g) {
+      const int tn = (g & 1) ? 256 : 128, mh = (g & 2) ? 2 : 1;
+      std::vector<DenseJob> gj;
+      std::vector<int> gi;
       for (size_t k = 0; k < jobs.size(); ++k)
-        if (nj[k]) need[(size_t)job_of[k]] = 1;
+        if (job_tn[k] == tn && job_mh[k] == mh) {
+          gj.push_back(jobs[k]);
+          gi.push_back(job_of[k]);
+        }
+      if (gj.empty()) continue;
+      std::unique_ptr<bool[]> nj(new bool[gj.size()]);
+      dense_batch_needs_zero(gj.data(), (int)gj.size(), tn, sms, mh, nj.get());
+      for (size_t k = 0; k < gj.size(); ++k)
+        if (nj[k]) need[(size_t)gi[k]] = 1;
     }
     for (int32_t i = 0; i < count; ++i) {
       if (!active[(size_t)i]) continue;
@@ -611,8 +631,13 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
       zeroed[(size_t)i] = 1;
     }
   }
-  if (!jobs.empty()) {
-    rosko_status s = dense_batch_launch(jobs.data(), (int)jobs.size(), TN, sms, MH, st);
+  for (int g = 0; g < 4; ++g) {
+    const int tn = (g & 1) ? 256 : 128, mh = (g & 2) ? 2 : 1;
+    std::vector<DenseJob> gj;
+    for (size_t k = 0; k < jobs.size(); ++k)
+      if (job_tn[k] == tn && job_mh[k] == mh) gj.push_back(jobs[k]);
+    if (gj.empty()) continue;
+    rosko_status s = dense_batch_launch(gj.data(), (int)gj.size(), tn, sms, mh, st);
     if (s != ROSKO_OK) return s;
   }
   // sparse remainders (the dense tiles were launched above): the row-direct
@@ -687,8 +712,18 @@ static rosko_status spmm_dispatch(rosko_packed_t A, const void* B_dev, rosko_dty
     }
     if (!have && mode == ROSKO_SCHED_LEARNED) {
       rosko_status s = select_learned(A, N, &chosen, st);
-      if (s == ROSKO_OK) have = true;
-      else if (s != ROSKO_ERR_UNSUPPORTED) return s;
+      if (s == ROSKO_OK) {
+        have = true;
+      } else if (s == ROSKO_ERR_UNSUPPORTED) {
+        // no network, or features outside its training range: the analytic
+        // rule, remembered like a learned choice (later calls, e.g. under
+        // stream capture, neither recompute the features nor allocate)
+        std::memset(&chosen, 0, sizeof(chosen));
+        chosen.mode = ROSKO_SCHED_ANALYTIC;
+        have = true;
+      } else {
+        return s;
+      }
     }
     if (have) {
       {
@@ -696,7 +731,7 @@ static rosko_status spmm_dispatch(rosko_packed_t A, const void* B_dev, rosko_dty
         A->sched_cache[N * 4 + mode] = chosen;
       }
       return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,
-                      &chosen, st, flags);
+                      chosen.mode == ROSKO_SCHED_ANALYTIC ? nullptr : &chosen, st, flags);
     }
     // no cached choice and none can be made here: the analytic rule
     return spmm_run(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, accumulate,

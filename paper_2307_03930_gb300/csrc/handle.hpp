@@ -196,7 +196,7 @@ rosko_status spmm_validate(rosko_packed_s* A, const void* B_dev, rosko_dtype b_d
                            bool* done);
 // Nonzeros per row-direct work segment (longer rows are cut and their pieces
 // added into C atomically).
-constexpr int kSegRecords = 128;
+constexpr int kSegRecords = 64;
 constexpr int kRunSkipDense = 1;
 constexpr int kRunZeroed = 2;
 constexpr int kRunPlanOnly = 4;   // resolve the schedule, launch nothing (rosko_spmm_plan)

@@ -77,6 +77,7 @@ struct DenseTable {
   int count;
   int64_t units;
   int stages;
+  int aligned;   // CTA ranges start and end on tile boundaries (no tile is cut)
   int* status;
 };
 
@@ -89,6 +90,17 @@ __device__ __forceinline__ int64_t unit_begin(int64_t U, int64_t b, int64_t G) {
 template <int NP>
 __device__ __forceinline__ void advance_problem(const DenseTable<NP>& T, int64_t u, int& q) {
   while (q + 1 < T.count && u >= T.p[q + 1].unit0) ++q;
+}
+
+// First tile boundary at or after unit x (tile = `slabs` consecutive units).
+template <int NP>
+__device__ __forceinline__ int64_t tile_boundary(const DenseTable<NP>& T, int64_t x) {
+  if (x >= T.units) return T.units;
+  int q = 0;
+  advance_problem(T, x, q);
+  const int64_t slabs = T.p[q].slabs;
+  const int64_t r = (x - T.p[q].unit0) % slabs;
+  return r ? x + (slabs - r) : x;
 }
 
 // Position of a unit inside the batch: problem q, row-tile group mt, column
@@ -162,8 +174,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t u0 = unit_begin(T.units, blockIdx.x, gridDim.x);
-  const int64_t u1 = unit_begin(T.units, blockIdx.x + 1, gridDim.x);
+  int64_t u0 = unit_begin(T.units, blockIdx.x, gridDim.x);
+  int64_t u1 = unit_begin(T.units, blockIdx.x + 1, gridDim.x);
+  if (T.aligned) {
+    // many tiles: whole tiles per CTA (no zero fill, no reductions into C)
+    u0 = tile_boundary(T, u0);
+    u1 = tile_boundary(T, u1);
+  }
   if (u0 >= u1) return;
 
   if (threadIdx.x == 32) {
@@ -362,38 +379,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             ++chunk;
             continue;
           }
-          if (row >= P.M) continue;
-          float* dst = P.C + row * P.ldc + col0;
-          const bool vec = P.vec_ok && col0 + 32 <= P.N;
-          if (!whole) {
-            // a K range of a split tile: add into C (zeroed beforehand unless
-            // the call accumulates)
-            if (vec) {
+          // C rows not 16-byte aligned (no tensor map): transpose the 32 x 32
+          // chunk through this warp's staging tile (rotated rows, no bank
+          // conflicts) so that each store instruction writes 32 consecutive
+          // columns of one row
+          float* tr = reinterpret_cast<float*>(my_stage);
+          __syncwarp();
 #pragma unroll
-              for (int j = 0; j < 32; j += 4)
-                atomicAdd(reinterpret_cast<float4*>(dst + j),
-                          make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                      __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])));
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (col0 + j < P.N) atomicAdd(dst + j, __uint_as_float(r[j]));
+          for (int j = 0; j < 32; ++j) tr[lane * 32 + ((j + lane) & 31)] = __uint_as_float(r[j]);
+          __syncwarp();
+          const int64_t col = col0 + lane;
+          const int rows = (int)(P.M - row0 < 32 ? P.M - row0 : 32);
+          if (col < P.N) {
+#pragma unroll 4
+            for (int rr = 0; rr < rows; ++rr) {
+              const float v = tr[rr * 32 + ((lane + rr) & 31)];
+              float* dst = P.C + (row0 + rr) * P.ldc + col;
+              if (add) atomicAdd(dst, v);   // a cut tile, or C += A.B
+              else *dst = v;
             }
-          } else if (vec) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                     __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-              if (P.accumulate) {
-                const float4 o = *reinterpret_cast<const float4*>(dst + j);
-                v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
-              }
-              *reinterpret_cast<float4*>(dst + j) = v;
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (col0 + j < P.N) dst[j] = __uint_as_float(r[j]) + (P.accumulate ? dst[j] : 0.0f);
           }
         }
       }
@@ -494,6 +498,23 @@ rosko_status encode_dense_maps(const DenseJob& j, int MH, CUtensorMap* mA, CUten
   return ROSKO_OK;
 }
 
+// Tile-granular split when there are at least two tiles per CTA: the
+// stream-K balance is then not needed and uncut tiles need no zero fill of C
+// and no reductions.
+static bool use_aligned(int64_t tiles, int64_t G) { return tiles >= 2 * G; }
+
+// Stream-K pieces shorter than this many K slabs cost more in reductions
+// (every piece adds its partial tile into C) than they gain in balance.
+constexpr int64_t kMinUnitsPerCta = 8;
+
+// CTAs of a launch over `units` (tile, slab) units in `tiles` tiles: one per
+// SM at most, and no stream-K piece shorter than kMinUnitsPerCta slabs.
+static int64_t grid_for(int64_t units, int64_t tiles, int ctas) {
+  int64_t G = std::min<int64_t>(ctas, units);
+  if (!use_aligned(tiles, G)) G = std::min<int64_t>(G, std::max(tiles, units / kMinUnitsPerCta));
+  return std::max<int64_t>(1, G);
+}
+
 template <int TN, int NP, int MH>
 rosko_status run_jobs(const DenseJob* jobs, int count, int ctas, cudaStream_t st) {
   static_assert(sizeof(DenseTable<NP>) <= 32 * 1024 - 256, "kernel parameter table too large");
@@ -528,10 +549,13 @@ rosko_status run_jobs(const DenseJob* jobs, int count, int ctas, cudaStream_t st
   if (n == 0) return ROSKO_OK;
   T.count = n;
   T.units = units;
+  int64_t tiles = 0;
+  for (int i = 0; i < n; ++i) tiles += (int64_t)((T.p[i].n_copy + MH - 1) / MH) * T.p[i].n_ntiles;
+  const int64_t grid = grid_for(units, tiles, ctas);
+  T.aligned = use_aligned(tiles, grid) ? 1 : 0;
   T.stages = dense_stages<TN, MH>();
   T.status = device_status_word();
   if (!T.status) return ROSKO_ERR_CUDA;
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ctas, units));
   return launch_table<TN, NP, MH>(T, grid, st);
 }
 
@@ -542,7 +566,8 @@ static int64_t job_units(int64_t n_tiles, int64_t N, int64_t K, int TN, int MH) 
 }
 
 int64_t dense_grid(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas, int MH) {
-  return std::max<int64_t>(1, std::min<int64_t>(ctas, job_units(n_tiles, N, K, TN, MH)));
+  const int64_t units = job_units(n_tiles, N, K, TN, MH);
+  return grid_for(units, units / slabs_of(K), ctas);
 }
 
 // True when the stream-K split of `units` over `ctas` CTAs cuts some tile of
@@ -560,6 +585,7 @@ static bool split_cuts_tile(int64_t units_before, int64_t units, int64_t total, 
 bool dense_needs_zero(int64_t n_tiles, int64_t N, int64_t K, int TN, int ctas, int MH) {
   const int64_t units = job_units(n_tiles, N, K, TN, MH);
   const int64_t G = dense_grid(n_tiles, N, K, TN, ctas, MH);
+  if (use_aligned(units / slabs_of(K), G)) return false;
   return split_cuts_tile(0, units, units, slabs_of(K), G);
 }
 
@@ -570,10 +596,16 @@ void dense_batch_needs_zero(const DenseJob* jobs, int count, int TN, int ctas, i
   for (int i = 0; i < count; ++i)
     if (jobs[i].n_tiles > 0 && jobs[i].N > 0)
       total += job_units(jobs[i].n_tiles, jobs[i].N, jobs[i].K, TN, MH);
-  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(ctas, total));
+  int64_t tiles = 0;
+  for (int i = 0; i < count; ++i)
+    if (jobs[i].n_tiles > 0 && jobs[i].N > 0)
+      tiles += job_units(jobs[i].n_tiles, jobs[i].N, jobs[i].K, TN, MH) / slabs_of(jobs[i].K);
+  const int64_t G = grid_for(total, tiles, ctas);
+  const bool aligned = use_aligned(tiles, G);
   int64_t before = 0;
   for (int i = 0; i < count; ++i) {
     out[i] = false;
+    if (aligned) continue;
     if (jobs[i].n_tiles <= 0 || jobs[i].N <= 0) continue;
     const int64_t units = job_units(jobs[i].n_tiles, jobs[i].N, jobs[i].K, TN, MH);
     out[i] = split_cuts_tile(before, units, total, slabs_of(jobs[i].K), G);

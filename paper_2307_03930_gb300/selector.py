@@ -28,23 +28,38 @@ WEIGHTS = os.path.join(HERE, "selector_weights.npz")
 PATTERNS = ("uniform", "block4x1", "powerlaw")
 
 
-def random_problems(seed: int, count: int):
+def random_problems(seed: int, count: int, family: str = "layers"):
     """(M, K, N, s, pattern, matrix seed) per problem; draw order M, K, N, s,
-    pattern."""
+    pattern.
+
+    family "layers": M, K log-uniform in [64, 4096], N log-uniform in
+    [196, 12544], s uniform in [0.70, 0.99] (the held-out distribution).
+    family "conv": convolution-shaped layers, M = output channels
+    log-uniform in [64, 2048], K = 9 x input channels (log-uniform in
+    [32, 1024]), N = output pixels log-uniform in [196, 12544], s uniform in
+    [0.5, 0.999] (magnitude-pruned density range of a pruned network) -
+    training only, so that the network also covers deeper, denser and
+    sparser layers than the held-out family."""
     from . import inputs as gen
-    rng = gen.rng_for(seed, 0)
+    rng = gen.rng_for(seed, 0 if family == "layers" else 1)
     out = []
     for i in range(count):
-        M = gen.loguniform_int(rng, 64, 4096)
-        K = gen.loguniform_int(rng, 64, 4096)
-        N = gen.loguniform_int(rng, 196, 12544)
-        s = float(rng.uniform(0.70, 0.99))
+        if family == "layers":
+            M = gen.loguniform_int(rng, 64, 4096)
+            K = gen.loguniform_int(rng, 64, 4096)
+            N = gen.loguniform_int(rng, 196, 12544)
+            s = float(rng.uniform(0.70, 0.99))
+        else:
+            M = gen.loguniform_int(rng, 64, 2048)
+            K = 9 * gen.loguniform_int(rng, 32, 1024)
+            N = gen.loguniform_int(rng, 196, 12544)
+            s = float(rng.uniform(0.5, 0.999))
         pat = PATTERNS[int(rng.integers(0, len(PATTERNS)))]
         out.append((M, K, N, s, pat, i))
     return out
 
 
-def sweep(seed: int, count: int, reps: int = 3, log_every: int = 50):
+def sweep(seed: int, count: int, reps: int = 3, log_every: int = 50, family: str = "layers"):
     """Features, per-candidate times (NaN where a candidate does not apply)
     and the analytic rule's time for `count` random problems."""
     import torch
@@ -58,8 +73,8 @@ def sweep(seed: int, count: int, reps: int = 3, log_every: int = 50):
     analytic = np.zeros(count)
     meta = []
     t0 = time.time()
-    for j, (M, K, N, s, pat, i) in enumerate(random_problems(seed, count)):
-        A = gen.sparse_weight(M, K, s, gen.rng_for(seed, 1, i), pat)
+    for j, (M, K, N, s, pat, i) in enumerate(random_problems(seed, count, family)):
+        A = gen.sparse_weight(M, K, s, gen.rng_for(seed, 1 if family == "layers" else 3, i), pat)
         h = rosko.rosko_pack(torch.from_numpy(A).to(dev), rosko.BF16)
         ldb = -(-N // 8) * 8
         Bbuf = torch.randn((K, ldb), device=dev, dtype=torch.bfloat16)
@@ -189,6 +204,8 @@ def main():
     ap.add_argument("--seed", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--data-in", default=None, help="train on a saved sweep (npz) instead")
+    ap.add_argument("--extra", type=int, default=0,
+                    help="also sweep this many convolution-shaped training problems")
     ap.add_argument("--heldout-out", default=None,
                     help="save the held-out split (features, times, analytic) as npz")
     ap.add_argument("--out", default=WEIGHTS)
@@ -202,6 +219,10 @@ def main():
     else:
         tr = sweep(a.seed, a.train)
         ho = sweep(a.seed + 1000, a.heldout)
+    if a.extra:
+        ex = sweep(a.seed, a.extra, family="conv")
+        tr = {k: (np.concatenate([tr[k], ex[k]]) if k != "meta" else tr.get(k, []) + ex[k])
+              for k in ("features", "times", "analytic")}
     if a.heldout_out:
         np.savez_compressed(a.heldout_out, features=ho["features"].astype(np.float32),
                             times=ho["times"].astype(np.float32),

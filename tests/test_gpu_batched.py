@@ -1,5 +1,5 @@
-"""Batched SpMM (one persistent stream-K tensor-core launch for every
-problem's dense tiles, one row-direct launch for the row-direct sparse
+"""Batched SpMM (one persistent tensor-core launch per CTA-tile shape for
+every problem's dense tiles, one row-direct launch for the row-direct sparse
 remainders, other remainders per problem) against the oracle, and its
 capture/replay in a CUDA graph.  GPU only."""
 import numpy as np
@@ -33,7 +33,7 @@ def _run_batched(rosko, probs, tiles=None, accumulate=False, C0s=None, f32=False
     code, bt, esz = (rosko.F32, torch.float32, 4) if f32 else (rosko.BF16, torch.bfloat16, 2)
     hs = [rosko.rosko_pack(torch.from_numpy(A).cuda(), code) for A, _ in probs]
     Bs = [_ldpad(torch.from_numpy(B).to(bt), esz) for _, B in probs]
-    Cs = [torch.zeros((A.shape[0], B.shape[1]), device="cuda") for A, B in probs]
+    Cs = [torch.full((A.shape[0], B.shape[1]), float("nan"), device="cuda") for A, B in probs]
     if C0s is not None:
         for C, C0 in zip(Cs, C0s):
             C.copy_(torch.from_numpy(C0))
@@ -56,8 +56,9 @@ def test_batched_matches_oracle(accumulate):
         if accumulate:
             D = D + np.abs(C0s[j])
         assert normalized_error(C.cpu().numpy(), ref, D) <= 1e-5, j
-    # one dense launch for all problems + at most one sparse launch per problem
-    assert launches <= 1 + len(probs)
+    # one dense launch per CTA-tile shape (at most four) + one row-direct
+    # launch for every sparse remainder
+    assert launches <= 5
 
 
 @pytest.mark.parametrize("MC", [128, 256])
@@ -69,8 +70,9 @@ def test_batched_forced_dense_for_all(MC):
     for (A, B), C in zip(probs, Cs):
         ref, D = spmm(bf16_round(A), bf16_round(B))
         assert normalized_error(C.cpu().numpy(), ref, D) <= 1e-5
-    # every tile has density >= 1 per mille except the 99.9% problem's
-    assert launches <= 2
+    # every tile has density >= 1 per mille except the 99.9% problem's:
+    # two tile shapes here (small K: 128 columns) + one row-direct launch
+    assert launches <= 3
 
 
 def test_batched_graph_capture_and_replay():

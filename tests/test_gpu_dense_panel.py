@@ -19,7 +19,9 @@ def _run(rosko, A, B, tile, rows=None, accumulate=False, C0=None, dense_min_pm=0
     N = B.shape[1]
     h = rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16, dense_min_pm=dense_min_pm)
     Bd = _ldpad(torch.from_numpy(B).to(torch.bfloat16), 2)
-    C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    # C = A.B overwrites C: start from NaN so that an element no kernel
+    # writes (or a missed zero fill) fails the comparison
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
     if C0 is not None:
         C.copy_(torch.from_numpy(C0))
     l0 = rosko.rosko_kernel_launches()
@@ -136,3 +138,19 @@ def test_plan_reports_the_split_and_launches_nothing():
     # sparse only: no dense tile
     pl = rosko.rosko_spmm_plan(h, B, C, tile=rosko.make_tile(dense_split_pm=1001))
     assert pl["dense_tiles"] == 0 and pl["sparse_panels"] == -(-1000 // 16)
+
+
+@pytest.mark.parametrize("ctas,TN,MC", [(5, 128, 128), (16, 256, 128), (7, 128, 256)])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_tile_aligned_split(ctas, TN, MC, accumulate):
+    # at least four tiles per CTA: each CTA owns whole tiles (stored, not
+    # reduced; C is not zero-filled first)
+    rosko = built()
+    A = gen.sparse_weight(1000, 300, 0.6, gen.rng_for(17), "uniform")
+    B = gen.normal((300, 1000), gen.rng_for(18))
+    C0 = np.random.default_rng(4).standard_normal((1000, 1000)).astype(np.float32) \
+        if accumulate else None
+    t = rosko.make_tile(dense_split_pm=1, dense_n_r=TN, dense_split_k=ctas, dense_m_c=MC)
+    err, launches = _run(rosko, A, B, t, accumulate=accumulate, C0=C0)
+    assert err <= 1e-5, err
+    assert launches == 1

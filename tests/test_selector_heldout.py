@@ -1,0 +1,92 @@
+"""The trained selector against the analytic rule on the 2,000 held-out
+problems of the measurement sweep (every candidate timed on a GB300, stored
+beside the weights).  The network's choices are recomputed here with the FP64
+oracle MLP from the shipped weights, so the claim is checked on CPU; a GPU
+test checks that the library's own forward kernel picks the same candidates."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from tests._lib import ROOT
+from oracle import mlp as omlp
+
+PKG = os.path.join(ROOT, "paper_2307_03930_gb300")
+WEIGHTS = os.path.join(PKG, "selector_weights.npz")
+HELDOUT = os.path.join(PKG, "selector_heldout.npz")
+
+
+def _load():
+    w = np.load(WEIGHTS, allow_pickle=False)
+    h = np.load(HELDOUT, allow_pickle=False)
+    return w, h
+
+
+def _unflat(v, n_in, n_out):
+    sizes = [n_in, 64, 64, 64, n_out]
+    out, off = [], 0
+    for l in range(4):
+        W = v[off:off + sizes[l] * sizes[l + 1]].reshape(sizes[l + 1], sizes[l])
+        off += W.size
+        b = v[off:off + sizes[l + 1]]
+        off += b.size
+        out += [W.astype(np.float64), b.astype(np.float64)]
+    assert off == v.size
+    return out
+
+
+def _choices(w, feats, applicable):
+    X = (feats.astype(np.float64) - w["mean"]) / w["std"]
+    n_out = applicable.shape[1]
+    z, _ = omlp.forward(_unflat(w["params"], feats.shape[1], n_out), X)
+    z = np.where(applicable, z, -np.inf)
+    return np.argmax(z, axis=1), z
+
+
+def test_heldout_files_are_complete():
+    w, h = _load()
+    t = h["times"]
+    assert t.shape[0] == 2000 and h["features"].shape == (2000, 16)
+    assert h["analytic"].shape == (2000,)
+    # every held-out problem was timed under every applicable candidate
+    assert np.all(np.isfinite(np.nanmin(t, axis=1)))
+    info = json.loads(str(w["info"]))
+    assert info["heldout"]["n"] == 2000
+
+
+def test_learned_selector_beats_the_analytic_rule_on_heldout_problems():
+    w, h = _load()
+    t = h["times"].astype(np.float64)
+    ok = np.isfinite(t)
+    choice, _ = _choices(w, h["features"], ok)
+    best = np.nanmin(t, axis=1)
+    chosen = t[np.arange(len(t)), choice]
+    mlp_regret = np.mean(chosen / best - 1.0)
+    analytic_regret = np.mean(h["analytic"] / best - 1.0)
+    # mean regret (t_chosen / t_best - 1) against exhaustive search
+    assert mlp_regret < analytic_regret, (mlp_regret, analytic_regret)
+    # and the network's picks are faster than the rule's (geometric mean)
+    gain = np.exp(np.mean(np.log(h["analytic"] / chosen)))
+    assert gain > 1.0, gain
+
+
+@pytest.mark.gpu
+def test_gpu_forward_picks_the_same_candidates():
+    import torch
+    from tests._lib import built
+    rosko = built()
+    if not (os.path.exists(WEIGHTS) and os.path.exists(HELDOUT)):
+        pytest.skip("no trained selector shipped (the CPU tests fail on that)")
+    w, h = _load()
+    ok = np.isfinite(h["times"])
+    want, z_ref = _choices(w, h["features"], ok)
+    X = ((h["features"] - w["mean"]) / w["std"]).astype(np.float32)
+    z = rosko.rosko_mlp_forward(torch.from_numpy(w["params"]).cuda(),
+                                torch.from_numpy(X).cuda(), ok.shape[1]).cpu().numpy()
+    z = np.where(ok, z, -np.inf)
+    got = np.argmax(z, axis=1)
+    # FP32 against FP64: agree except where the top two logits nearly tie
+    zs = np.sort(np.where(ok, z_ref, -np.inf), axis=1)
+    clear = (zs[:, -1] - zs[:, -2]) > 1e-3
+    assert np.array_equal(got[clear], want[clear])

@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--impl", default="rosko", choices=["rosko", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the FP32/cuSPARSE/cuBLAS comparison legs")
+                    help="skip the comparison legs (FP32, cuSPARSE, cuBLAS, batched, other "
+                         "schedules)")
     ap.add_argument("--case", type=float, default=None,
                     help="profiling: run only the SpMM of this sparsity (BF16 and FP32 forms)")
     ap.add_argument("--autotune", action="store_true",
@@ -347,14 +348,15 @@ def main():
     # analytic rule, the learned selector, the per-shape autotuner (its search
     # runs on the first, uncaptured call of each handle and is cached)
     forms_ms = {"analytic": graph_time(lambda: step(0, tl=rosko.make_tile()), torch, reps=20)}
-    if learned_ok:
+    if learned_ok and not args.no_extras:
         forms_ms["learned"] = graph_time(lambda: step(0, tl=rosko.make_tile(mode=rosko.SCHED_LEARNED)),
                                          torch, reps=20)
         forms_ms["learned_choices"] = [rosko.rosko_spmm_plan(
             handles16[i], sets[0]["B16"][i], sets[0]["C"][i],
             tile=rosko.make_tile(mode=rosko.SCHED_LEARNED))["tile"] for i in range(len(SPARSITIES))]
-    forms_ms["autotune"] = graph_time(lambda: step(0, tl=rosko.make_tile(mode=rosko.SCHED_AUTOTUNE)),
-                                      torch, reps=20)
+    if not args.no_extras:
+        forms_ms["autotune"] = graph_time(
+            lambda: step(0, tl=rosko.make_tile(mode=rosko.SCHED_AUTOTUNE)), torch, reps=20)
 
     # ---------------- per-sparsity figures and the roofline -------------------
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -413,6 +415,7 @@ def main():
     if not args.no_extras:
         extras = comparison_legs(rosko, torch, dev, sets, infos, stream)
         extras["batched_uneven_layers"] = batched_leg(rosko, torch, dev)
+        extras["pack"] = pack_leg(rosko, torch, dev, sets)
 
     # ---------------- end to end: host buffers through the C-ABI -----------------
     e2e = end_to_end(rosko, torch, dev, sets, handles16, stream, flops_step, world, tile=tile)
@@ -542,6 +545,30 @@ def _time(fn, torch, stream, reps=20, warm=3):
     return a.elapsed_time(b) / reps
 
 
+def pack_leg(rosko, torch, dev, sets):
+    """Device pack (Alg. 1, BF16 with dense copies) of each A of the sweep
+    against cuSPARSE's dense -> CSR conversion (torch.to_sparse_csr) of the
+    same FP32 matrix (the inspector cost of dynamic sparsity, Sec. 4.1);
+    wall time per conversion, synchronised (the pack reads its sizes back)."""
+    out = []
+    for i, s in enumerate(SPARSITIES):
+        A32 = torch.from_numpy(sets[0]["A_np"][i]).to(dev)
+        ts = {}
+        for name, fn in (("rosko_pack_bf16", lambda: rosko.rosko_pack(A32, rosko.BF16)),
+                         ("rosko_pack_f32", lambda: rosko.rosko_pack(A32, rosko.F32)),
+                         ("cusparse_dense_to_csr", lambda: A32.to_sparse_csr())):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(5):
+                r = fn()
+                torch.cuda.synchronize()
+                del r
+            ts[name + "_ms"] = (time.perf_counter() - t0) / 5 * 1e3
+        out.append({"sparsity": s, **ts})
+    return out
+
+
 def comparison_legs(rosko, torch, dev, sets, infos, stream):
     """Plain FP32 form, cuSPARSE CSR and cuBLAS dense on the same shapes.  Each
     timed call cycles through the six distinct B buffers of one input set
@@ -636,32 +663,54 @@ def end_to_end(rosko, torch, dev, sets, handles, stream, flops_step, world, step
     """Same metric through the C-ABI with pinned host buffers: per step the six
     B inputs are copied host->device, the SpMMs run, and the six C results are
     copied back (the packed weights stay resident, as for pre-packed inference
-    weights, Sec. 4.1)."""
+    weights, Sec. 4.1).  Three streams pipeline the layers: layer i+1's input
+    copy and layer i-1's result copy overlap layer i's SpMM (events order
+    each buffer's copy-in, SpMM and copy-out, also across steps)."""
     hB = [[torch.from_numpy(b).to(torch.bfloat16).pin_memory() for b in S["B_np"]] for S in sets]
     hC = [torch.empty((M, N), dtype=torch.float32).pin_memory() for _ in SPARSITIES]
     dB = [torch.empty((K, N), dtype=torch.bfloat16, device=dev) for _ in SPARSITIES]
     dC = [torch.empty((M, N), dtype=torch.float32, device=dev) for _ in SPARSITIES]
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    n = len(SPARSITIES)
+    ev_in = [torch.cuda.Event() for _ in range(n)]     # B_i on the device
+    ev_mm = [torch.cuda.Event() for _ in range(n)]     # SpMM_i done (B_i free, C_i ready)
+    ev_out = [torch.cuda.Event() for _ in range(n)]    # C_i copied back (C_i free)
+    for i in range(n):
+        for e in (ev_mm[i], ev_out[i]):
+            e.record(stream)
 
     def one(t):
-        for i in range(len(SPARSITIES)):
-            dB[i].copy_(hB[t % 2][i], non_blocking=True)
-            rosko.rosko_spmm(handles[i], dB[i], dC[i], tile=tile)
-            hC[i].copy_(dC[i], non_blocking=True)
+        for i in range(n):
+            s_in.wait_event(ev_mm[i])              # previous step's SpMM_i read B_i
+            with torch.cuda.stream(s_in):
+                dB[i].copy_(hB[t % 2][i], non_blocking=True)
+                ev_in[i].record(s_in)
+            stream.wait_event(ev_in[i])
+            stream.wait_event(ev_out[i])           # previous step's C_i copied out
+            rosko.rosko_spmm(handles[i], dB[i], dC[i], tile=tile, stream=stream)
+            ev_mm[i].record(stream)
+            s_out.wait_event(ev_mm[i])
+            with torch.cuda.stream(s_out):
+                hC[i].copy_(dC[i], non_blocking=True)
+                ev_out[i].record(s_out)
 
     for t in range(3):
         one(t)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
+    s_in.wait_event(a)
     for t in range(steps):
         one(t)
+    stream.wait_stream(s_out)
+    stream.wait_stream(s_in)
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     return {"value": world * flops_step / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
-            "h2d_bytes_per_step": len(SPARSITIES) * K * N * 2,
-            "d2h_bytes_per_step": len(SPARSITIES) * M * N * 4, "ms_per_step": ms,
-            "steps": steps}
+            "h2d_bytes_per_step": n * K * N * 2,
+            "d2h_bytes_per_step": n * M * N * 4, "ms_per_step": ms,
+            "steps": steps, "pipelining": "3 streams (copy-in, SpMM, copy-out)"}
 
 
 if __name__ == "__main__":

@@ -143,6 +143,20 @@ rosko_status rosko_pack(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64
                         const rosko_tile* tile, rosko_stream_t stream, rosko_packed_t* out);
 
 /*
+ * rosko_pack_transposed - rosko_pack of the K x M transpose of the dense
+ * row-major M x K matrix A_dev, for the other SpMM of a pruned layer's
+ * training step (the input gradient W^T . dO of Sec. 5.4's CNN training).  Same
+ * rules as rosko_pack with the roles of M and K exchanged (I8-from-I8 row
+ * scales are per row of the transpose, i.e. per column of A).  A K x M
+ * scratch copy is allocated for the transpose and freed before returning;
+ * synchronises `stream`.
+ */
+rosko_status rosko_pack_transposed(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64_t K,
+                                   int64_t lda, rosko_dtype packed_dtype,
+                                   const float* row_scale_dev, const rosko_tile* tile,
+                                   rosko_stream_t stream, rosko_packed_t* out);
+
+/*
  * rosko_spmm - C = A.B (accumulate = 0) or C += A.B (accumulate = 1, the
  * in-place accumulation of Alg. 2, which loads C first).
  *
@@ -264,6 +278,12 @@ int32_t rosko_num_candidates(void);
  * does not apply to this handle (e.g. a dense split on a non-BF16 pack).
  */
 rosko_status rosko_candidate(rosko_packed_t A, int64_t N, int32_t index, rosko_tile* out);
+/* Index of the candidate with the schedule of `tile` (e.g. the analytic
+ * rule's, from rosko_schedule_analytic; tile->m_r = the handle's panel
+ * height) for handles of packed_dtype, or -1 if no candidate has it.  Host
+ * only.  ROSKO_SCHED_LEARNED keeps the analytic rule unless the network's
+ * logit for its pick exceeds this candidate's by ln 2. */
+int32_t rosko_candidate_index(const rosko_tile* tile, rosko_dtype packed_dtype);
 
 /*
  * rosko_autotune - per-shape search (Sec. 6: the tile parameters are exposed

@@ -274,6 +274,31 @@ rosko_status rosko_pack(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64
   return ROSKO_OK;
 }
 
+rosko_status rosko_pack_transposed(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64_t K,
+                                   int64_t lda, rosko_dtype packed_dtype,
+                                   const float* row_scale_dev, const rosko_tile* tile,
+                                   rosko_stream_t stream, rosko_packed_t* out) {
+  if (!out) return ROSKO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!dtype_valid(a_dtype)) return ROSKO_ERR_INVALID_ARG;
+  if (M < 0 || K < 0 || lda < std::max<int64_t>(K, 1)) return ROSKO_ERR_INVALID_ARG;
+  if (M * K > 0 && !A_dev) return ROSKO_ERR_INVALID_ARG;
+  if (M > 0 && K > 0 && M > (int64_t)INT32_MAX / K) return ROSKO_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // dense transpose (K x M, leading dimension M) in scratch, then Alg. 1 on it
+  void* t = nullptr;
+  const size_t bytes = (size_t)std::max<int64_t>(M * K, 1) * dtype_size(a_dtype);
+  if (dev_malloc(&t, bytes) != cudaSuccess) return ROSKO_ERR_OOM;
+  rosko_status s = transpose_impl(A_dev, a_dtype, M, K, lda, t, st);
+  if (s == ROSKO_OK)
+    s = rosko_pack(t, a_dtype, K, M, std::max<int64_t>(M, 1), packed_dtype, row_scale_dev, tile,
+                   stream, out);
+  // the pack synchronised the stream: the scratch is no longer read
+  cudaStreamSynchronize(st);
+  cudaFree(t);
+  return s;
+}
+
 void rosko_free(rosko_packed_t A) {
   if (!A || A->magic != kHandleMagic) return;
   A->magic = 0;
@@ -899,6 +924,11 @@ rosko_status rosko_time_tile(rosko_packed_t A, const void* B_dev, rosko_dtype b_
   *ms = time_tile(A, B_dev, b_dtype, N, ldb, col_scale_dev, C_dev, c_dtype, ldc, tile, reps, st,
                   &err);
   return err;
+}
+
+int32_t rosko_candidate_index(const rosko_tile* tile, rosko_dtype packed_dtype) {
+  if (!tile || !dtype_valid(packed_dtype) || tile->m_r <= 0) return -1;
+  return candidate_index(tile, packed_dtype);
 }
 
 rosko_status rosko_features(rosko_packed_t A, int64_t N, double* features16,

@@ -68,6 +68,34 @@ bool candidate_tile(const rosko_packed_s* h, int64_t N, int idx, rosko_tile* t) 
   return true;
 }
 
+// Index of the candidate with the schedule of tile t (same traversal, columns
+// per lane, dense threshold and, for the slab traversals, CTA height, slab
+// depth and K split), or -1; t->m_r is the handle's panel height.
+int candidate_index(const rosko_tile* t, rosko_dtype dt) {
+  for (int i = 0; i < num_candidates(); ++i) {
+    const SparseCand& sc = kSparse[i / kNumDense];
+    if (sc.order != t->order || kDensePm[i % kNumDense] != t->dense_split_pm) continue;
+    const int V = sc.V > 0 ? sc.V : sparse_default_V(dt, t->m_r, sc.order);
+    if (32 * V != t->n_r) continue;
+    if (sc.order != 4) {
+      const int W = sc.order == 3 ? 128 / t->m_r : sc.W;
+      if (W * t->m_r != t->m_c || sc.KC != t->k_c || sc.split != t->split_k) continue;
+    }
+    return i;
+  }
+  return -1;
+}
+
+// The applicable candidate whose schedule is the analytic rule's for this
+// handle and width, or -1.
+int analytic_candidate(const rosko_packed_s* h, int64_t N) {
+  rosko_tile a;
+  schedule_analytic(h->M, h->K, N, h->nnz, h->m_r, h->dt, num_sms(), &a);
+  const int i = candidate_index(&a, h->dt);
+  rosko_tile t;
+  return (i >= 0 && candidate_tile(h, N, i, &t)) ? i : -1;
+}
+
 rosko_status spmm_forced(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N, int64_t ldb,
                          const float* col_scale, void* C, rosko_dtype c_dt, int64_t ldc,
                          const rosko_tile* t, cudaStream_t st);

@@ -113,6 +113,8 @@ constexpr int kDenseTileRows = 128;
 rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
                        rosko_dtype p_dt, const float* row_scale_in, int32_t m_r,
                        int32_t dense_min_pm, cudaStream_t stream, rosko_packed_s** out);
+rosko_status transpose_impl(const void* A, rosko_dtype dt, int64_t M, int64_t K, int64_t lda,
+                            void* out, cudaStream_t st);
 rosko_status unpack_impl(rosko_packed_s* h, void* A_out, int64_t lda, cudaStream_t stream);
 rosko_status count_nonzeros(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
                             cudaStream_t st, int64_t* out);
@@ -217,6 +219,8 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
 // autotune.cu
 int num_candidates();
 bool candidate_tile(const rosko_packed_s* h, int64_t N, int idx, rosko_tile* t);
+int analytic_candidate(const rosko_packed_s* h, int64_t N);
+int candidate_index(const rosko_tile* t, rosko_dtype dt);
 rosko_status autotune_impl(rosko_packed_s* h, const void* B, rosko_dtype b_dt, int64_t N,
                            int64_t ldb, const float* col_scale, void* C, rosko_dtype c_dt,
                            int64_t ldc, int reps, rosko_tile* best, float* times,

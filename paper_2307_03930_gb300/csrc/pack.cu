@@ -771,7 +771,46 @@ rosko_status build_segments(rosko_packed_s* h, const std::vector<int32_t>* panel
   return ROSKO_OK;
 }
 
+// out[c][r] = in[r][c] for an R x C matrix of E-byte elements (row-major,
+// leading dimensions ld_in / ld_out); 32 x 32 tiles through shared memory.
+template <class E>
+__global__ void transpose_kernel(const E* __restrict__ in, int64_t R, int64_t C, int64_t ld_in,
+                                 E* __restrict__ out, int64_t ld_out) {
+  __shared__ E tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t r = r0 + j, c = c0 + threadIdx.x;
+    if (r < R && c < C) tile[j][threadIdx.x] = in[r * ld_in + c];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t c = c0 + j, r = r0 + threadIdx.x;
+    if (r < R && c < C) out[c * ld_out + r] = tile[threadIdx.x][j];
+  }
+}
+
 }  // namespace
+
+// Dense K x M transpose of a row-major M x K matrix into `out` (ld = M).
+rosko_status transpose_impl(const void* A, rosko_dtype dt, int64_t M, int64_t K, int64_t lda,
+                            void* out, cudaStream_t st) {
+  if (M == 0 || K == 0) return ROSKO_OK;
+  const dim3 grid((unsigned)((K + 31) / 32), (unsigned)((M + 31) / 32));
+  if (grid.y > 65535) return ROSKO_ERR_INVALID_ARG;
+  const dim3 block(32, 8);
+  const size_t es = dtype_size(dt);
+  if (es == 4)
+    transpose_kernel<uint32_t><<<grid, block, 0, st>>>(static_cast<const uint32_t*>(A), M, K, lda,
+                                                       static_cast<uint32_t*>(out), M);
+  else if (es == 2)
+    transpose_kernel<uint16_t><<<grid, block, 0, st>>>(static_cast<const uint16_t*>(A), M, K, lda,
+                                                       static_cast<uint16_t*>(out), M);
+  else
+    transpose_kernel<uint8_t><<<grid, block, 0, st>>>(static_cast<const uint8_t*>(A), M, K, lda,
+                                                      static_cast<uint8_t*>(out), M);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+}
 
 rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
                        rosko_dtype p_dt, const float* row_scale_in, int32_t m_r,

@@ -485,6 +485,14 @@ rosko_status select_learned(rosko_packed_s* h, int64_t N, rosko_tile* out, cudaS
     if (best < 0 || z[(size_t)c] > z[(size_t)best]) best = c;
   }
   if (best < 0) return ROSKO_ERR_UNSUPPORTED;
+  // The analytic rule stays unless the network prefers another candidate by
+  // a clear margin: its logit must exceed that of the candidate matching the
+  // rule's schedule by ln 2 (the network rates it at least twice as likely to
+  // be the fastest).  Without such a candidate the network decides alone.
+  const int eq = analytic_candidate(h, N);
+  if (eq >= 0 && eq != best && z[(size_t)best] - z[(size_t)eq] <= 0.6931472f)
+    return ROSKO_ERR_UNSUPPORTED;
+  if (eq == best) return ROSKO_ERR_UNSUPPORTED;
   candidate_tile(h, N, best, out);
   out->mode = ROSKO_SCHED_FORCED;
   return ROSKO_OK;

@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
         "rosko_status_string": (ctypes.c_char_p, [ci]),
         "rosko_pack": (ci, [vp, ci, i64, i64, i64, ci, vp, P_tile, vp, ctypes.POINTER(vp)]),
         "rosko_spmm": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, ci, P_tile, vp]),
+        "rosko_pack_transposed": (ci, [vp, ci, i64, i64, i64, ci, vp, P_tile, vp,
+                                       ctypes.POINTER(vp)]),
         "rosko_spmm_plan": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, ci, P_tile,
                                  ctypes.POINTER(rosko_plan), vp]),
         "rosko_free": (None, [vp]),
@@ -96,6 +98,7 @@ def lib() -> ctypes.CDLL:
         "rosko_time_tile": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, P_tile, i32,
                                  ctypes.POINTER(ctypes.c_float), vp]),
         "rosko_features": (ci, [vp, i64, ctypes.POINTER(ctypes.c_double), vp]),
+        "rosko_candidate_index": (i32, [P_tile, ci]),
         "rosko_features_static": (ci, [vp, i64, vp, vp]),
         "rosko_mlp_param_count": (i64, [i32, i32]),
         "rosko_mlp_workspace_floats": (i64, [i64, i32]),
@@ -137,8 +140,12 @@ def _ptr(t: Optional[torch.Tensor]):
 
 
 def _ld(t: torch.Tensor) -> int:
-    if t.dim() != 2 or t.stride(1) != 1:
+    """Leading dimension of a row-major 2-D tensor (the stride of a size-1
+    dimension carries no layout and is ignored)."""
+    if t.dim() != 2 or (t.size(1) > 1 and t.stride(1) != 1):
         raise ValueError("row-major 2-D tensor with unit column stride expected")
+    if t.size(0) <= 1:
+        return max(int(t.stride(0)), int(t.size(1)), 1)
     return int(t.stride(0))
 
 
@@ -180,6 +187,23 @@ def rosko_pack(A: torch.Tensor, packed_dtype: int, m_r: int = 0,
                       ctypes.c_void_p(_stream(stream)), ctypes.byref(out))
     _check(st, "rosko_pack")
     return PackedA(out.value, M, K)
+
+
+def rosko_pack_transposed(A: torch.Tensor, packed_dtype: int, m_r: int = 0,
+                          row_scale: Optional[torch.Tensor] = None, stream=None,
+                          dense_min_pm: int = 0) -> PackedA:
+    """Alg. 1 on the device applied to the transpose of the dense row-major A
+    (the handle is K x M)."""
+    L = lib()
+    M, K = A.shape
+    lda = _ld(A) if A.numel() else max(K, 1)
+    tile = make_tile(m_r=m_r, dense_split_pm=dense_min_pm)
+    out = ctypes.c_void_p()
+    st = L.rosko_pack_transposed(_ptr(A) if A.numel() else None, TORCH_TO_CODE[A.dtype], M, K,
+                                 lda, int(packed_dtype), _ptr(row_scale), ctypes.byref(tile),
+                                 ctypes.c_void_p(_stream(stream)), ctypes.byref(out))
+    _check(st, "rosko_pack_transposed")
+    return PackedA(out.value, K, M)
 
 
 def rosko_spmm(A: PackedA, B: torch.Tensor, C: torch.Tensor,
@@ -262,6 +286,26 @@ def rosko_schedule_analytic(M: int, K: int, N: int, nnz: int, m_r: int = 0,
     _check(lib().rosko_schedule_analytic(M, K, N, nnz, m_r, packed_dtype, ctypes.byref(t)),
            "rosko_schedule_analytic")
     return t.as_dict()
+
+
+def rosko_candidate_index(tile, packed_dtype: int) -> int:
+    """Candidate index of a tile (rosko_tile or its dict), -1 if none."""
+    if isinstance(tile, dict):
+        tile = make_tile(**tile)
+    return int(lib().rosko_candidate_index(ctypes.byref(tile), int(packed_dtype)))
+
+
+def analytic_candidates(features, packed_dtype: int = BF16, m_r: int = 16):
+    """Per feature row (log2 M, log2 K, log2 N, density, ...): the index of
+    the candidate matching the analytic rule's schedule, -1 if none."""
+    import numpy as np
+    out = np.full(len(features), -1, dtype=np.int64)
+    for i, f in enumerate(np.asarray(features, dtype=np.float64)):
+        M, K, N = (int(round(2.0 ** f[j])) for j in range(3))
+        nnz = int(round(f[3] * M * K))
+        t = rosko_schedule_analytic(M, K, N, nnz, m_r, packed_dtype)
+        out[i] = rosko_candidate_index(t, packed_dtype)
+    return out
 
 
 def rosko_device_status(clear: bool = False) -> int:

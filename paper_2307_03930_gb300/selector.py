@@ -153,9 +153,25 @@ def train(features: np.ndarray, times: np.ndarray, epochs: int = 200, lr: float 
             "lo": features.min(axis=0), "hi": features.max(axis=0), "losses": losses}
 
 
+MARGIN = float(np.log(2.0))   # the library's deference margin (logit units)
+
+
+def choose(z: np.ndarray, applicable: np.ndarray, eq: np.ndarray) -> np.ndarray:
+    """The library's learned-mode choice from logits z: the argmax over the
+    applicable candidates, unless it beats the candidate matching the
+    analytic rule (eq, -1 if none) by at most MARGIN; then -1 (= the rule)."""
+    z = np.where(applicable, z, -np.inf)
+    top = np.argmax(z, axis=1)
+    rows = np.arange(len(z))
+    has = eq >= 0
+    zeq = np.where(has, z[rows, np.maximum(eq, 0)], -np.inf)
+    defer = has & ((top == eq) | (z[rows, top] - zeq <= MARGIN))
+    return np.where(defer, -1, top)
+
+
 def predict(model: dict, features: np.ndarray, applicable: np.ndarray) -> np.ndarray:
-    """Chosen candidate per row: argmax of the GPU network's logits over the
-    applicable candidates."""
+    """Chosen candidate per row as the library's learned mode picks it (-1:
+    the analytic rule), from the GPU network's logits."""
     import torch
 
     from . import rosko
@@ -163,15 +179,16 @@ def predict(model: dict, features: np.ndarray, applicable: np.ndarray) -> np.nda
     nc = applicable.shape[1]
     z = rosko.rosko_mlp_forward(torch.from_numpy(model["params"]).cuda(),
                                 torch.from_numpy(X).cuda(), nc).cpu().numpy()
-    z[~applicable] = -np.inf
-    return np.argmax(z, axis=1)
+    return choose(z, applicable, rosko.analytic_candidates(features))
 
 
 def regret(times: np.ndarray, analytic: np.ndarray, choice: np.ndarray) -> dict:
     """Mean of t_chosen / t_best - 1 for the network and for the analytic rule,
-    and the geometric-mean speedup of the network's choice over the rule."""
+    and the geometric-mean speedup of the network's choice over the rule
+    (choice -1 = the analytic rule's own time)."""
     best = np.nanmin(times, axis=1)
-    chosen = times[np.arange(times.shape[0]), choice]
+    chosen = np.where(choice >= 0, times[np.arange(times.shape[0]), np.maximum(choice, 0)],
+                      analytic)
     return {"mlp_regret": float(np.mean(chosen / best - 1.0)),
             "analytic_regret": float(np.mean(analytic / best - 1.0)),
             "mlp_vs_analytic_geomean_speedup": float(np.exp(np.mean(np.log(analytic / chosen)))),

@@ -5,6 +5,7 @@ import pytest
 import torch
 
 from tests._lib import built
+from paper_2307_03930_gb300 import inputs as gen
 from oracle.pack import pack_panels
 from oracle.quant import bf16_bits, bf16_round, quantize_rows_int8
 
@@ -129,3 +130,23 @@ def test_alloc_failure_is_reported(monkeypatch):
     monkeypatch.delenv("ROSKO_FAIL_ALLOC")
     h = rosko.rosko_pack(A, 0)
     assert h.info()["nnz"] == int((A != 0).sum())
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16", "i8"])
+@pytest.mark.parametrize("M,K", [(300, 177), (1, 64), (129, 1)])
+def test_pack_transposed_is_the_pack_of_the_transpose(dt, M, K):
+    # the backward SpMM of a pruned layer uses W^T: packing A transposed
+    # equals packing the transpose (byte-exact export), and the SpMM with it
+    # matches the oracle on A^T
+    rosko = built()
+    from tests.test_gpu_spmm import run, check
+    A = gen.sparse_weight(M, K, 0.8, gen.rng_for(91, M, K), "uniform")
+    code = {"f32": rosko.F32, "bf16": rosko.BF16, "i8": rosko.I8}[dt]
+    h1 = rosko.rosko_pack_transposed(torch.from_numpy(A).cuda(), code)
+    h2 = rosko.rosko_pack(torch.from_numpy(np.ascontiguousarray(A.T)).cuda(), code)
+    e1, e2 = rosko.rosko_packed_export(h1), rosko.rosko_packed_export(h2)
+    for k in e2:
+        assert np.array_equal(np.asarray(e1[k]), np.asarray(e2[k])), k
+    assert h1.info() == h2.info()
+    B = gen.normal((M, 70), gen.rng_for(92, M))
+    check(dt, *run(rosko, np.ascontiguousarray(A.T), B, dt, m_r=0))

@@ -1,8 +1,11 @@
 """The trained selector against the analytic rule on the 2,000 held-out
 problems of the measurement sweep (every candidate timed on a GB300, stored
 beside the weights).  The network's choices are recomputed here with the FP64
-oracle MLP from the shipped weights, so the claim is checked on CPU; a GPU
-test checks that the library's own forward kernel picks the same candidates."""
+oracle MLP from the shipped weights and the library's learned-mode rule (the
+network's pick unless it beats the analytic rule's candidate by at most ln 2
+in logit, see rosko_candidate_index), so the claim is checked on CPU; a GPU
+test checks that the library's own forward kernel picks the same
+candidates."""
 import json
 import os
 
@@ -56,19 +59,29 @@ def test_heldout_files_are_complete():
 
 
 def test_learned_selector_beats_the_analytic_rule_on_heldout_problems():
+    from tests._lib import built
+    from paper_2307_03930_gb300.selector import choose
+    rosko = built()   # host-only calls: the analytic rule's candidate
     w, h = _load()
     t = h["times"].astype(np.float64)
+    a = h["analytic"].astype(np.float64)
     ok = np.isfinite(t)
-    choice, _ = _choices(w, h["features"], ok)
+    _, z = _choices(w, h["features"], ok)
+    eq = rosko.analytic_candidates(h["features"])
+    assert np.mean(eq >= 0) > 0.99            # the rule's schedule is a candidate
+    choice = choose(z, ok, eq)
     best = np.nanmin(t, axis=1)
-    chosen = t[np.arange(len(t)), choice]
+    chosen = np.where(choice >= 0, t[np.arange(len(t)), np.maximum(choice, 0)], a)
     mlp_regret = np.mean(chosen / best - 1.0)
-    analytic_regret = np.mean(h["analytic"] / best - 1.0)
+    analytic_regret = np.mean(a / best - 1.0)
     # mean regret (t_chosen / t_best - 1) against exhaustive search
     assert mlp_regret < analytic_regret, (mlp_regret, analytic_regret)
-    # and the network's picks are faster than the rule's (geometric mean)
-    gain = np.exp(np.mean(np.log(h["analytic"] / chosen)))
+    # and the learned mode's picks are faster than the rule's (geometric mean)
+    gain = np.exp(np.mean(np.log(a / chosen)))
     assert gain > 1.0, gain
+    # the network alone (no deference to the rule) is better than the rule too
+    top, _ = _choices(w, h["features"], ok)
+    assert np.mean(t[np.arange(len(t)), top] / best - 1.0) < analytic_regret
 
 
 @pytest.mark.gpu

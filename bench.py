@@ -357,6 +357,11 @@ def main():
     if not args.no_extras:
         forms_ms["autotune"] = graph_time(
             lambda: step(0, tl=rosko.make_tile(mode=rosko.SCHED_AUTOTUNE)), torch, reps=20)
+        # the six independent layers as one rosko_spmm_batched call (one
+        # tensor-core launch for the five dense layers, one row-direct launch)
+        forms_ms["batched_call"] = graph_time(
+            lambda: rosko.rosko_spmm_batched(handles16, sets[0]["B16"], sets[0]["C"]), torch,
+            reps=20)
 
     # ---------------- per-sparsity figures and the roofline -------------------
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -416,6 +421,7 @@ def main():
         extras = comparison_legs(rosko, torch, dev, sets, infos, stream)
         extras["batched_uneven_layers"] = batched_leg(rosko, torch, dev)
         extras["pack"] = pack_leg(rosko, torch, dev, sets)
+        extras["other_configs"] = other_configs_leg(rosko, torch, dev)
 
     # ---------------- end to end: host buffers through the C-ABI -----------------
     e2e = end_to_end(rosko, torch, dev, sets, handles16, stream, flops_step, world, tile=tile)
@@ -543,6 +549,47 @@ def _time(fn, torch, stream, reps=20, warm=3):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def other_configs_leg(rosko, torch, dev):
+    """The other fixed configurations, analytic schedule, CUDA-event graph
+    timing with cycled B (> L2): plain FP32 1024 x 1024 x 1024 at 90%
+    (uniform, seed 0), and the transformer-FFN shapes 11008 x 4096 and
+    4096 x 11008 (K x 2048 tokens, magnitude-pruned at 70/90/95%, seed 2) in
+    BF16 -> FP32 and INT8 -> INT32."""
+    from paper_2307_03930_gb300 import inputs as gen
+    out = {}
+    rng = gen.rng_for(0)
+    A = gen.sparse_weight(1024, 1024, 0.9, rng, "uniform")
+    h = rosko.rosko_pack(torch.from_numpy(A).to(dev), rosko.F32)
+    Bs = [torch.randn((1024, 1024), device=dev) for _ in range(40)]   # 160 MB
+    Cs = [torch.empty((1024, 1024), device=dev) for _ in range(40)]
+    ms = cycled_time(lambda j: rosko.rosko_spmm(h, Bs[j], Cs[j]), torch, reps=40, n_buf=40)
+    out["c1_fp32_1024_s90"] = {"us": ms * 1e3, "gflops": 2.0 * h.info()["nnz"] * 1024 / ms / 1e6}
+    del Bs, Cs, h
+    for (Mx, Kx) in ((11008, 4096), (4096, 11008)):
+        for s in (0.7, 0.9, 0.95):
+            rng = gen.rng_for(2, Mx, int(round(s * 100)))
+            A = gen.magnitude_prune(gen.normal((Mx, Kx), rng), s)
+            Ad = torch.from_numpy(A).to(dev)
+            nb = 3
+            B16 = [torch.randn((Kx, 2048), device=dev).to(torch.bfloat16) for _ in range(nb)]
+            B8 = [torch.randint(-127, 128, (Kx, 2048), device=dev, dtype=torch.int8)
+                  for _ in range(nb)]
+            C32 = [torch.empty((Mx, 2048), device=dev) for _ in range(nb)]
+            C32i = [torch.empty((Mx, 2048), device=dev, dtype=torch.int32) for _ in range(nb)]
+            h16 = rosko.rosko_pack(Ad, rosko.BF16)
+            h8 = rosko.rosko_pack(Ad, rosko.I8)
+            nnz = h16.info()["nnz"]
+            key = f"c3_{Mx}x{Kx}x2048_s{int(round(s * 100))}"
+            t16 = cycled_time(lambda j: rosko.rosko_spmm(h16, B16[j], C32[j]), torch, reps=6,
+                              n_buf=nb)
+            t8 = cycled_time(lambda j: rosko.rosko_spmm(h8, B8[j], C32i[j]), torch, reps=6,
+                             n_buf=nb)
+            out[key] = {"bf16_us": t16 * 1e3, "bf16_gflops": 2.0 * nnz * 2048 / t16 / 1e6,
+                        "int8_us": t8 * 1e3, "int8_gops": 2.0 * h8.info()["nnz"] * 2048 / t8 / 1e6}
+            del Ad, B16, B8, C32, C32i, h16, h8
+    return out
 
 
 def pack_leg(rosko, torch, dev, sets):

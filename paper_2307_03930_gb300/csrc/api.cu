@@ -194,14 +194,20 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
     // d >= 5 per mille) and keep the layer sparse when row-direct is
     // predicted faster.  Dense: work at ~0.8 PFLOP/s.  Row-direct: nnz * N
     // BF16 values from L2 at ~5 TB/s, plus its latency chain: a warp walks
-    // one row piece (<= kSegRecords nonzeros) four records per ~0.8 us
+    // one row piece (of the length picked below) four records per ~0.8 us
     // round trip, and ~24 warps per SM are resident.
     const double t_dense = 6.0 + 2.0 * (double)M * (double)K * (double)N / 0.8e15 * 1e6;
     const double row = M ? (double)nnz / (double)M : 0.0;
-    const double pieces = std::max(1.0, std::ceil(row / kSegRecords));
-    const double warps = (double)M * pieces * std::ceil((double)N / 256.0);
+    // the piece length a launch would pick (coarse if it still gives four
+    // waves of resident warps, else kSegRecords)
+    const double strips = std::ceil((double)N / 256.0);
+    double seg = (double)seg_records_for(nnz, M);
+    if ((double)M * std::max(1.0, std::ceil(row / seg)) * strips < 4.0 * 24.0 * sms)
+      seg = kSegRecords;
+    const double pieces = std::max(1.0, std::ceil(row / seg));
+    const double warps = (double)M * pieces * strips;
     const double waves = std::ceil(warps / (24.0 * sms));
-    const double chain = 0.8 * std::ceil(std::min(row, (double)kSegRecords) / 4.0) * waves;
+    const double chain = 0.8 * std::ceil(std::min(row, seg) / 4.0) * waves;
     const double t_direct = 3.0 + (double)nnz * (double)N * 2.0 / 5e12 * 1e6 + chain;
     if (t_direct < t_dense) t->dense_split_pm = 1001;
   }
@@ -485,7 +491,8 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
   bool direct_cut = false;
   if (L.order == 4 && n_sparse > 0) {
     int64_t ns = 0;
-    if (!direct_segments(A, A->panel_order_dev, n_sparse, &ns, &direct_cut))
+    const int which = direct_pick(A, A->panel_order_dev, n_sparse, N, L.V);
+    if (!direct_segments(A, A->panel_order_dev, n_sparse, which, &ns, &direct_cut))
       return ROSKO_ERR_UNSUPPORTED;
   }
   const bool zero_c =
@@ -616,8 +623,10 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
       r.split_k = 1;   // row-direct: no K split, but cut rows add into C
       int64_t ns = 0;
       bool cut = false;
-      if (A[i]->rnz && direct_segments(A[i], A[i]->panel_order_dev, A[i]->P - dp, &ns, &cut) &&
-          cut)
+      const int V = r.n_r > 0 ? r.n_r / 32 : sparse_default_V(A[i]->dt, A[i]->m_r, 4);
+      const int which = direct_pick(A[i], A[i]->panel_order_dev, A[i]->P - dp, N[i], V);
+      if (A[i]->rnz &&
+          direct_segments(A[i], A[i]->panel_order_dev, A[i]->P - dp, which, &ns, &cut) && cut)
         direct_cut[(size_t)i] = 1;
     }
     rest[(size_t)i] = r;

@@ -1,6 +1,8 @@
 // Packed-A handle shared by the pack, SpMM and API translation units.
 #pragma once
 
+#include <algorithm>
+
 #include <stdint.h>
 
 #include <map>
@@ -33,6 +35,16 @@ constexpr int kNumFeatures = 16;
 //                    record whose k (0xFFFF / INT32_MAX) ends the row:
 //                      BF16, INT8: uint32 = value bits << 16 | k
 //                      FP32: uint2 {k, value bits}; FP64: {double, k, pad}
+// Row-direct work segments: a row longer than twice the mean row length (and
+// than kSegRecords) is cut into pieces of that length whose sums are added
+// into C atomically, so that power-law rows do not serialise on one warp
+// while rows of an even matrix stay whole.
+constexpr int kSegRecords = 64;
+inline int64_t seg_records_for(int64_t nnz, int64_t M) {
+  const int64_t twice_mean = M > 0 ? (2 * nnz + M - 1) / M : 0;
+  return std::max<int64_t>(kSegRecords, (twice_mean + 31) / 32 * 32);
+}
+
 struct rosko_packed_s {
   uint64_t magic = 0;
   int device = 0;
@@ -58,17 +70,23 @@ struct rosko_packed_s {
   int32_t* gu_k = nullptr;
   void* gnz = nullptr;
   int64_t gu_total = 0;
-  // Row-direct work segments (row stream only): each row is cut into pieces
-  // of at most kSegRecords nonzeros, {row, piece} per segment, in row order
-  // (seg_nat) and in panel_order order (seg_ord, BF16 packs with dense
-  // copies); seg_prefix[i] / split_prefix[i] count the segments / the panels
-  // with a cut row among the first i panels of panel_order (or of the
-  // natural order when there is no panel_order).
+  // Row-direct work segments (row stream only), at two granularities: list
+  // 0 cuts every row into pieces of at most kSegRecords nonzeros (many
+  // warps for few or long rows), list 1 only rows longer than
+  // seg_records_for (twice the mean; few atomics for even matrices).  Per
+  // list: {row, piece} per segment in row order (nat) and in panel_order
+  // order (ord, BF16 packs with dense copies); prefix[i] / split[i] count the
+  // segments / the panels with a cut row among the first i panels of
+  // panel_order (or of the natural order without one).
+  struct SegList {
+    int2* nat = nullptr;
+    int2* ord = nullptr;
+    std::vector<int64_t> prefix;
+    std::vector<int32_t> split;
+    int32_t records = kSegRecords;
+  };
+  SegList segs[2];
   void* seg_base = nullptr;
-  int2* seg_nat = nullptr;
-  int2* seg_ord = nullptr;
-  std::vector<int64_t> seg_prefix;
-  std::vector<int32_t> split_prefix;
   float* feat_dev = nullptr;   // kNumFeatures floats (N-independent part)
   int64_t* panel_nnz_dev = nullptr;  // P+1 nonzero offsets of panels
   // Dense-panel split (BF16 only).  128-row tiles sorted by density,
@@ -162,7 +180,11 @@ struct DirectJob {
 // (their sums are added into C, which must then be zeroed unless the call
 // accumulates).
 const int2* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
-                            int64_t* n_segs, bool* cut);
+                            int which, int64_t* n_segs, bool* cut);
+// The list a launch over these panels with width N and V columns per lane
+// uses (0 fine, 1 coarse); decided the same way for zero-fill and launch.
+int direct_pick(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels, int64_t N,
+                int V);
 // One launch over all jobs (count <= 64, same handle / B / C types, V
 // columns per lane); C of jobs with cut rows must be zeroed by the caller
 // unless they accumulate.
@@ -196,9 +218,6 @@ rosko_status spmm_validate(rosko_packed_s* A, const void* B_dev, rosko_dtype b_d
                            int64_t ldb, const float* col_scale_dev, void* C_dev,
                            rosko_dtype c_dtype, int64_t ldc, int accumulate, cudaStream_t st,
                            bool* done);
-// Nonzeros per row-direct work segment (longer rows are cut and their pieces
-// added into C atomically).
-constexpr int kSegRecords = 64;
 constexpr int kRunSkipDense = 1;
 constexpr int kRunZeroed = 2;
 constexpr int kRunPlanOnly = 4;   // resolve the schedule, launch nothing (rosko_spmm_plan)

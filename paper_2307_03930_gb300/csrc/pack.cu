@@ -722,7 +722,7 @@ rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pm, ro
 }
 
 // Row-direct work segments (see rosko_packed_s): built on the host from the
-// row pointers, once per pack.
+// row pointers, once per pack, at both granularities.
 rosko_status build_segments(rosko_packed_s* h, const std::vector<int32_t>* panel_order,
                             cudaStream_t st) {
   const int64_t M = h->M, P = h->P;
@@ -731,43 +731,57 @@ rosko_status build_segments(rosko_packed_s* h, const std::vector<int32_t>* panel
   if (cudaStreamSynchronize(st) != cudaSuccess ||
       cudaMemcpy(rp.data(), h->rowptr, (size_t)(M + 1) * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
     return ROSKO_ERR_CUDA;
-  std::vector<int2> nat;
-  nat.reserve((size_t)M + (size_t)(h->nnz / kSegRecords) + 1);
-  std::vector<int64_t> panel_seg((size_t)P + 1, 0);
-  std::vector<char> panel_split((size_t)P, 0);
-  for (int64_t p = 0; p < P; ++p) {
-    panel_seg[(size_t)p] = (int64_t)nat.size();
-    for (int64_t r = p * h->m_r; r < std::min<int64_t>(M, (p + 1) * h->m_r); ++r) {
-      const int64_t nr = (int64_t)rp[(size_t)r + 1] - rp[(size_t)r] - 1;   // minus the sentinel
-      const int64_t ns = std::max<int64_t>(1, (nr + kSegRecords - 1) / kSegRecords);
-      if (ns > 1) panel_split[(size_t)p] = 1;
-      for (int64_t k = 0; k < ns; ++k) nat.push_back(make_int2((int)r, (int)k));
+  const int64_t lens[2] = {kSegRecords, seg_records_for(h->nnz, M)};
+  std::vector<int2> nat[2], ord[2];
+  for (int g = 0; g < 2; ++g) {
+    const int64_t seg = lens[g];
+    rosko_packed_s::SegList& L = h->segs[g];
+    L.records = (int32_t)seg;
+    nat[g].reserve((size_t)M + (size_t)(h->nnz / seg) + 1);
+    std::vector<int64_t> panel_seg((size_t)P + 1, 0);
+    std::vector<char> panel_split((size_t)P, 0);
+    for (int64_t p = 0; p < P; ++p) {
+      panel_seg[(size_t)p] = (int64_t)nat[g].size();
+      for (int64_t r = p * h->m_r; r < std::min<int64_t>(M, (p + 1) * h->m_r); ++r) {
+        const int64_t nr = (int64_t)rp[(size_t)r + 1] - rp[(size_t)r] - 1;   // minus the sentinel
+        const int64_t ns = std::max<int64_t>(1, (nr + seg - 1) / seg);
+        if (ns > 1) panel_split[(size_t)p] = 1;
+        for (int64_t k = 0; k < ns; ++k) nat[g].push_back(make_int2((int)r, (int)k));
+      }
+    }
+    panel_seg[(size_t)P] = (int64_t)nat[g].size();
+    L.prefix.assign((size_t)P + 1, 0);
+    L.split.assign((size_t)P + 1, 0);
+    for (int64_t i = 0; i < P; ++i) {
+      const int64_t p = panel_order ? (*panel_order)[(size_t)i] : i;
+      if (panel_order)
+        ord[g].insert(ord[g].end(), nat[g].begin() + panel_seg[(size_t)p],
+                      nat[g].begin() + panel_seg[(size_t)p + 1]);
+      L.prefix[(size_t)i + 1] = L.prefix[(size_t)i] + (panel_seg[(size_t)p + 1] - panel_seg[(size_t)p]);
+      L.split[(size_t)i + 1] = L.split[(size_t)i] + panel_split[(size_t)p];
     }
   }
-  panel_seg[(size_t)P] = (int64_t)nat.size();
-  std::vector<int2> ord;
-  h->seg_prefix.assign((size_t)P + 1, 0);
-  h->split_prefix.assign((size_t)P + 1, 0);
-  for (int64_t i = 0; i < P; ++i) {
-    const int64_t p = panel_order ? (*panel_order)[(size_t)i] : i;
-    if (panel_order)
-      ord.insert(ord.end(), nat.begin() + panel_seg[(size_t)p], nat.begin() + panel_seg[(size_t)p + 1]);
-    h->seg_prefix[(size_t)i + 1] = h->seg_prefix[(size_t)i] + (panel_seg[(size_t)p + 1] - panel_seg[(size_t)p]);
-    h->split_prefix[(size_t)i + 1] = h->split_prefix[(size_t)i] + panel_split[(size_t)p];
+  // one allocation: nat0, ord0, nat1, ord1
+  size_t off[4], total = 0;
+  for (int g = 0; g < 2; ++g) {
+    off[2 * g] = total;
+    total = align_up(total + nat[g].size() * sizeof(int2), 256);
+    off[2 * g + 1] = total;
+    total = align_up(total + (panel_order ? ord[g].size() * sizeof(int2) : 0), 256);
   }
-  const size_t n = nat.size();
-  const size_t o_ord = align_up(n * sizeof(int2), 256);
-  if (dev_malloc(&h->seg_base, o_ord + (panel_order ? n * sizeof(int2) : 0) + 256) != cudaSuccess)
-    return ROSKO_ERR_OOM;
-  h->seg_nat = static_cast<int2*>(h->seg_base);
-  h->seg_ord = panel_order ? reinterpret_cast<int2*>(static_cast<char*>(h->seg_base) + o_ord)
-                           : nullptr;
-  if (cudaMemcpyAsync(h->seg_nat, nat.data(), n * sizeof(int2), cudaMemcpyHostToDevice, st) !=
-          cudaSuccess ||
-      (panel_order && cudaMemcpyAsync(h->seg_ord, ord.data(), n * sizeof(int2),
-                                      cudaMemcpyHostToDevice, st) != cudaSuccess) ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
+  if (dev_malloc(&h->seg_base, total + 256) != cudaSuccess) return ROSKO_ERR_OOM;
+  char* base = static_cast<char*>(h->seg_base);
+  for (int g = 0; g < 2; ++g) {
+    rosko_packed_s::SegList& L = h->segs[g];
+    L.nat = reinterpret_cast<int2*>(base + off[2 * g]);
+    L.ord = panel_order ? reinterpret_cast<int2*>(base + off[2 * g + 1]) : nullptr;
+    if (cudaMemcpyAsync(L.nat, nat[g].data(), nat[g].size() * sizeof(int2),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (panel_order && cudaMemcpyAsync(L.ord, ord[g].data(), ord[g].size() * sizeof(int2),
+                                        cudaMemcpyHostToDevice, st) != cudaSuccess))
+      return ROSKO_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return ROSKO_ERR_CUDA;
   return ROSKO_OK;
 }
 

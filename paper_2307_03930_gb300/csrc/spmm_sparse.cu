@@ -482,8 +482,8 @@ __global__ void __launch_bounds__(288, 1)
 // that few or none of the CTA's nonzeros use, while here every B byte read
 // is used and all of B (resident in the 129 MB L2) serves every SM.
 // A row's records are fetched 32 at a time across the lanes and broadcast
-// by shuffles in batches of four, whose B loads are all issued before the
-// FMAs (batches of eight measured slower).
+// by shuffles in batches of four, whose B loads are all issued, into
+// registers of the storage type, before the FMAs.
 //
 // One launch serves a batch: the problems travel in the kernel parameters
 // and the blocks of problem q are [blocks0(q), blocks0(q+1)); a block is 8
@@ -504,6 +504,12 @@ __device__ __forceinline__ RecF64 shfl_rec(const RecF64& w, int src) {
   return o;
 }
 
+// A register type of exactly B bytes (4, 8 or 16) for raw chunk loads.
+template <int B> struct RawOf;
+template <> struct RawOf<4> { using type = uint32_t; };
+template <> struct RawOf<8> { using type = uint2; };
+template <> struct RawOf<16> { using type = uint4; };
+
 struct DirectProb {
   const int32_t* rowptr;      // row stream: per-row k-ascending records + sentinel
   const void* rnz;
@@ -515,6 +521,7 @@ struct DirectProb {
   int64_t n_segs, ldb, ldc, M, N;
   int64_t blocks0;            // first block of this problem
   int strips, load_c_first, add_c_at_end, vec_ok;
+  int seg_records;            // nonzeros per piece of a cut row
 };
 
 template <int NP>
@@ -524,14 +531,16 @@ struct DirectTable {
 };
 
 template <class TA, class TB, class TC, int V, int NP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     rowdirect_kernel(const __grid_constant__ DirectTable<NP> T) {
   using TACC = typename AccOf<TA>::type;
   using WT = typename RowRec<TA>::T;
   constexpr int G = (16 / (int)sizeof(TB)) < 8 ? (16 / (int)sizeof(TB)) : 8;
   constexpr int CE = V < G ? V : G;   // elements per lane chunk (<= 16 bytes)
   constexpr int J = V / CE;           // chunks per lane, 32 CE columns apart
-  constexpr int U = 4;                // records in flight per warp
+  // records in flight per warp (batches of eight measured slower for every
+  // B type)
+  constexpr int U = 4;
   static_assert(J * CE == V, "V must be a multiple of the chunk width");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int q = 0;
@@ -541,7 +550,7 @@ __global__ void __launch_bounds__(256)
   const int64_t strip = lb % P.strips;
   const int64_t w = (lb / P.strips) * 8 + warp;
   if (w >= P.n_segs) return;
-  // this warp's segment: piece `seg.y` (at most kSegRecords nonzeros) of row
+  // this warp's segment: piece `seg.y` (at most seg_records nonzeros) of row
   // `seg.x`; the pieces of a cut row are added into C atomically
   const int2 seg = __ldg(&P.segs[w]);
   const int64_t row = seg.x;
@@ -557,38 +566,53 @@ __global__ void __launch_bounds__(256)
   const WT* __restrict__ rnz = reinterpret_cast<const WT*>(P.rnz);
   const int r0 = __ldg(&P.rowptr[row]);
   const int r_end = __ldg(&P.rowptr[row + 1]) - 1;   // the last record is the sentinel
-  const bool cut = r_end - r0 > kSegRecords;
-  const int e0 = r0 + seg.y * kSegRecords;
-  const int e_end = min(e0 + kSegRecords, r_end);
+  const bool cut = r_end - r0 > P.seg_records;
+  const int e0 = r0 + seg.y * P.seg_records;
+  const int e_end = min(e0 + P.seg_records, r_end);
   const TB* bcol = static_cast<const TB*>(P.B) + n0 + lane * CE;
   const int64_t ldb = P.ldb, N = P.N;
-  auto load_b = [&](int k, TACC* b) {
+  // B chunks stay in their storage type until the FMAs (BF16 / INT8 take
+  // half / a quarter of the registers of their accumulator type), so more
+  // records' loads are in flight per warp
+  using RawT = typename RawOf<CE * (int)sizeof(TB)>::type;
+  auto load_raw = [&](int k, RawT* raw) {
     const TB* src = bcol + (int64_t)k * ldb;
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-      if (whole[j]) {
-        load_chunk<TB, TACC, CE>(src + j * 32 * CE, b + j * CE);
+    for (int jj = 0; jj < J; ++jj) {
+      if (whole[jj]) {
+        raw[jj] = *reinterpret_cast<const RawT*>(src + jj * 32 * CE);
       } else {
+        TB tmp[CE];
 #pragma unroll
         for (int v = 0; v < CE; ++v) {
-          const int64_t col = n0 + j * 32 * CE + lane * CE + v;
-          b[j * CE + v] = col < N ? to_acc(src[j * 32 * CE + v], TACC(0)) : TACC(0);
+          const int64_t col = n0 + jj * 32 * CE + lane * CE + v;
+          tmp[v] = col < N ? src[jj * 32 * CE + v] : TB(0);
         }
+        raw[jj] = *reinterpret_cast<const RawT*>(tmp);
       }
     }
   };
+  auto fma_raw = [&](TACC a, const RawT* raw) {
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+      const TB* vals = reinterpret_cast<const TB*>(&raw[jj]);
+#pragma unroll
+      for (int v = 0; v < CE; ++v)
+        acc[jj * CE + v] = mac(a, to_acc(vals[v], TACC(0)), acc[jj * CE + v]);
+    }
+  };
+  if (P.load_c_first && !cut) {
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj)
+#pragma unroll
+      for (int v = 0; v < CE; ++v) {
+        const int64_t col = n0 + jj * 32 * CE + lane * CE + v;
+        if (col < N) acc[jj * CE + v] = (TACC)crow[col];
+      }
+  }
   // 32 records at a time: lane i loads record i (one coalesced request),
   // then batches of U are broadcast by shuffles and their B loads issued
   // together, so a row costs few dependent round trips to memory
-  if (P.load_c_first && !cut) {
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-#pragma unroll
-      for (int v = 0; v < CE; ++v) {
-        const int64_t col = n0 + j * 32 * CE + lane * CE + v;
-        if (col < N) acc[j * CE + v] = (TACC)crow[col];
-      }
-  }
   for (int base = e0; base < e_end; base += 32) {
     const int cnt = min(32, e_end - base);
     WT mine;
@@ -596,24 +620,20 @@ __global__ void __launch_bounds__(256)
     else mine = rnz[e_end];               // the sentinel: never used
     for (int t = 0; t < cnt; t += U) {
       WT w[U];
-      TACC b[U][V];
+      RawT raw[U][J];
 #pragma unroll
       for (int u = 0; u < U; ++u) w[u] = shfl_rec(mine, t + u < cnt ? t + u : t);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (t + u < cnt) {
-          load_b(RowRec<TA>::k(w[u]), b[u]);
+          load_raw(RowRec<TA>::k(w[u]), raw[u]);
         } else {
 #pragma unroll
-          for (int v = 0; v < V; ++v) b[u][v] = TACC(0);
+          for (int jj = 0; jj < J; ++jj) raw[u][jj] = RawT{};
         }
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const TACC a = t + u < cnt ? RowRec<TA>::a(w[u]) : TACC(0);
-#pragma unroll
-        for (int v = 0; v < V; ++v) acc[v] = mac(a, b[u][v], acc[v]);
-      }
+      for (int u = 0; u < U; ++u) fma_raw(t + u < cnt ? RowRec<TA>::a(w[u]) : TACC(0), raw[u]);
     }
   }
   // C written once (dequantisation needs the scales of this problem)
@@ -768,31 +788,43 @@ int sparse_default_V(rosko_dtype p_dt, int R, int order) {
 }
 
 
-// The work segments of the listed panels (panel_list is NULL for all panels
-// in order, or the handle's panel_order with n_panels its first entries);
-// *n_segs receives their count (-1 for a list of another kind), *cut whether
-// one of those rows is cut into several pieces.
+// The work segments (list `which` of the handle, 0 = fine, 1 = coarse) of
+// the listed panels (panel_list is NULL for all panels in order, or the
+// handle's panel_order with n_panels its first entries); *n_segs receives
+// their count, *cut whether one of those rows is cut into several pieces.
+// NULL for a list of another kind.
 const int2* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
-                            int64_t* n_segs, bool* cut) {
+                            int which, int64_t* n_segs, bool* cut) {
   if (cut) *cut = false;
   *n_segs = -1;
-  if (!h->seg_nat || n_panels < 0 || n_panels > h->P) return nullptr;
+  const rosko_packed_s::SegList& L = h->segs[which & 1];
+  if (!L.nat || n_panels < 0 || n_panels > h->P) return nullptr;
   const int2* base;
   if (!panel_list) {
     // all panels in order (the prefix sums' last entry is the total in
     // either order)
     if (n_panels != h->P) return nullptr;
-    base = h->seg_nat;
-  } else if (panel_list == h->panel_order_dev && h->seg_ord) {
-    base = h->seg_ord;
+    base = L.nat;
+  } else if (panel_list == h->panel_order_dev && L.ord) {
+    base = L.ord;
   } else {
     return nullptr;
   }
-  *n_segs = h->seg_prefix[(size_t)n_panels];
-  if (cut) *cut = h->split_prefix[(size_t)n_panels] > 0;
+  *n_segs = L.prefix[(size_t)n_panels];
+  if (cut) *cut = L.split[(size_t)n_panels] > 0;
   return base;
 }
 
+// Granularity for a launch: the coarse list when it still gives every SM
+// four waves of resident warps (24 per SM) over the column strips, else the
+// fine list (more, shorter pieces; the cut rows are added atomically).
+int direct_pick(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels, int64_t N,
+                int V) {
+  int64_t ns = 0;
+  if (!direct_segments(h, panel_list, n_panels, 1, &ns, nullptr)) return 0;
+  const int64_t strips = (N + 32 * V - 1) / (32 * V);
+  return ns * strips >= 4LL * 24 * num_sms() ? 1 : 0;
+}
 
 // Fill one problem of a row-direct table; returns the problem's block count
 // (< 0: invalid argument).
@@ -802,7 +834,8 @@ static int64_t direct_prob(const DirectJob& j, int V, int64_t blocks0, DirectPro
   // 16-byte lane loads: B rows must start on 16-byte boundaries
   if (reinterpret_cast<uintptr_t>(j.B) % 16 != 0 || (j.ldb * (int64_t)bsz) % 16 != 0) return -1;
   int64_t n_segs = 0;
-  const int2* segs = direct_segments(h, j.panel_list, j.n_panels, &n_segs, nullptr);
+  const int which = direct_pick(h, j.panel_list, j.n_panels, j.N, V);
+  const int2* segs = direct_segments(h, j.panel_list, j.n_panels, which, &n_segs, nullptr);
   if (!segs) return -1;
   std::memset(P, 0, sizeof(*P));
   P->rowptr = h->rowptr;
@@ -818,6 +851,7 @@ static int64_t direct_prob(const DirectJob& j, int V, int64_t blocks0, DirectPro
   P->M = h->M;
   P->N = j.N;
   P->strips = (int)((j.N + 32 * V - 1) / (32 * V));
+  P->seg_records = h->segs[which].records;
   const bool dequant = (h->dt == ROSKO_I8 && j.c_dt == ROSKO_F32);
   P->load_c_first = j.accumulate && !dequant;
   P->add_c_at_end = j.accumulate && dequant;

@@ -267,3 +267,18 @@ def test_row_direct_cuts_long_rows(mode, accumulate):
               rng.standard_normal((M, N)).astype(np.float64 if mode == "f64" else np.float32))
     t = rosko.make_tile(order=4, dense_split_pm=1001)
     check(mode, *run(rosko, A, B, mode, m_r=16, tile=t, accumulate=accumulate, C0=C0))
+
+
+@pytest.mark.parametrize("mode", ["f32", "bf16", "i8"])
+def test_k_beyond_the_row_stream(mode):
+    # K >= 65280 does not fit the 16-bit k of the row stream: the pack builds
+    # no row stream and the library runs Alg. 2's column order (and, for
+    # BF16, the tensor-core path for dense-enough tiles)
+    rosko = built()
+    A, B = _problem(40, 70000, 33, 0.999, seed=95)
+    A[5, 65000:65100] = 1.5          # nonzeros past k = 65535
+    check(mode, *run(rosko, A, B, mode, m_r=0))
+    # forcing a row-stream traversal is refused, not silently wrong
+    t = rosko.make_tile(order=4, dense_split_pm=1001)
+    with pytest.raises(rosko.RoskoError):
+        run(rosko, A, B, mode, m_r=0, tile=t)

@@ -334,6 +334,7 @@ __global__ void row_count_kernel(const S* __restrict__ A, int64_t M, int64_t K, 
   if (row >= M) return;
   const float sc = scale ? scale[row] : 1.0f;
   int c = 0;
+#pragma unroll 8
   for (int64_t k = lane; k < K; k += 32) {
     D v;
     c += Conv<S, D>::get(A[row * lda + k], sc, v) ? 1 : 0;
@@ -354,13 +355,25 @@ __global__ void row_write_kernel(const S* __restrict__ A, int64_t M, int64_t K, 
   const float sc = scale ? scale[row] : 1.0f;
   int64_t pos = off[row].x;
   if (lane == 0) rowptr[row] = (int32_t)pos;
-  for (int64_t k0 = 0; k0 < K; k0 += 32) {
-    const int64_t k = k0 + lane;
-    D v;
-    const bool nzf = (k < K) && Conv<S, D>::get(A[row * lda + k], sc, v);
-    const unsigned mask = __ballot_sync(0xffffffffu, nzf);
-    if (nzf) put_row_rec(rnz, pos + __popc(mask & ((1u << lane) - 1u)), v, (int)k);
-    pos += __popc(mask);
+  // eight 32-column groups per step: their loads are issued together, then
+  // the records are written in k order
+  constexpr int G = 8;
+  for (int64_t k0 = 0; k0 < K; k0 += 32 * G) {
+    S a[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t k = k0 + g * 32 + lane;
+      a[g] = k < K ? A[row * lda + k] : S(0);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t k = k0 + g * 32 + lane;
+      D v;
+      const bool nzf = (k < K) && Conv<S, D>::get(a[g], sc, v);
+      const unsigned mask = __ballot_sync(0xffffffffu, nzf);
+      if (nzf) put_row_rec(rnz, pos + __popc(mask & ((1u << lane) - 1u)), v, (int)k);
+      pos += __popc(mask);
+    }
   }
   if (lane == 0) put_row_sentinel<D>(rnz, pos);
 }
@@ -375,9 +388,16 @@ __global__ void tile_flag_kernel(const S* __restrict__ A, int64_t M, int64_t K, 
   if (k >= K) return;
   const int64_t m0 = t * kDenseTileRows, m1 = min(M, m0 + kDenseTileRows);
   int any = 0;
-  for (int64_t m = m0; m < m1 && !any; ++m) {
-    D v;
-    any = Conv<S, D>::get(A[m * lda + k], scale ? scale[m] : 1.0f, v) ? 1 : 0;
+  // sixteen rows per step, loads issued together (no early exit, which would
+  // serialise them)
+  for (int64_t m = m0; m < m1; m += 16) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      if (m + u < m1) {
+        D v;
+        any |= Conv<S, D>::get(A[(m + u) * lda + k], scale ? scale[m + u] : 1.0f, v) ? 1 : 0;
+      }
+    }
   }
   flag[t * K + k] = make_int2(any, 0);
 }

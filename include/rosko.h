@@ -136,7 +136,10 @@ const char* rosko_status_string(rosko_status s);
  *         m_r <= 0: 16.
  * out     receives the new handle (set to NULL on error).
  * Zero test: IEEE a != 0, so -0.0 is dropped and NaN/Inf are kept.
- * Synchronises `stream` once to size the packed buffers.  M or K may be 0.
+ * Synchronises `stream` twice: once to size the packed buffers, and once
+ * before returning, so that the handle is ready for use on any stream.  Device
+ * memory (scratch and the handle) comes from the library's stream-ordered pool
+ * (see rosko_free).  M or K may be 0.
  */
 rosko_status rosko_pack(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64_t K,
                         int64_t lda, rosko_dtype packed_dtype, const float* row_scale_dev,
@@ -223,7 +226,12 @@ rosko_status rosko_spmm_batched(int32_t count, const rosko_packed_t* A, const vo
                                 const int64_t* ldc, rosko_dtype b_dtype, rosko_dtype c_dtype,
                                 int accumulate, const rosko_tile* tiles, rosko_stream_t stream);
 
-/* Release a packed handle and its device buffers.  NULL-safe. */
+/*
+ * Release a packed handle and its device buffers.  Waits for the handle's
+ * device to finish queued work (which may still read the handle), then
+ * returns the buffers to the library's memory pool on that device; the pool
+ * keeps up to 256 MiB of freed memory mapped for later packs.  NULL-safe.
+ */
 void rosko_free(rosko_packed_t A);
 
 /*

@@ -24,29 +24,72 @@ int g_sms[64] = {0};
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }  // namespace
 
-cudaError_t dev_malloc(void** p, size_t bytes) {
-  {
-    // Test hook: ROSKO_FAIL_ALLOC=n makes the n-th device allocation after the
-    // variable took its current value fail (host-side fault injection).
-    static std::string last;
-    static long since = 0;
-    std::lock_guard<std::mutex> lk(g_mu);
-    const char* f = std::getenv("ROSKO_FAIL_ALLOC");
-    if (!f) {
-      last.clear();
-      since = 0;
-    } else {
-      if (last != f) {
-        last = f;
-        since = 0;
-      }
-      if (std::atol(f) == ++since) {
-        *p = nullptr;
-        return cudaErrorMemoryAllocation;
-      }
-    }
+namespace {
+// Test hook: ROSKO_FAIL_ALLOC=n makes the n-th device allocation after the
+// variable took its current value fail (host-side fault injection).
+bool fail_alloc_hook() {
+  static std::string last;
+  static long since = 0;
+  std::lock_guard<std::mutex> lk(g_mu);
+  const char* f = std::getenv("ROSKO_FAIL_ALLOC");
+  if (!f) {
+    last.clear();
+    since = 0;
+    return false;
   }
+  if (last != f) {
+    last = f;
+    since = 0;
+  }
+  return std::atol(f) == ++since;
+}
+
+// Freed pool memory kept mapped for later packs, per device.
+constexpr uint64_t kPoolKeepBytes = 256ull << 20;
+cudaMemPool_t g_pool[64] = {};
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (fail_alloc_hook()) return cudaErrorMemoryAllocation;
   return cudaMalloc(p, bytes < 256 ? 256 : bytes);
+}
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (fail_alloc_hook()) return cudaErrorMemoryAllocation;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t created = nullptr;
+      e = cudaMemPoolCreate(&created, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = kPoolKeepBytes;
+      e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(created);
+        return e;
+      }
+      g_pool[dev] = created;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes < 256 ? 256 : bytes, pool, st);
+}
+
+void pool_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
 }
 
 namespace {
@@ -294,26 +337,29 @@ rosko_status rosko_pack_transposed(const void* A_dev, rosko_dtype a_dtype, int64
   // dense transpose (K x M, leading dimension M) in scratch, then Alg. 1 on it
   void* t = nullptr;
   const size_t bytes = (size_t)std::max<int64_t>(M * K, 1) * dtype_size(a_dtype);
-  if (dev_malloc(&t, bytes) != cudaSuccess) return ROSKO_ERR_OOM;
+  if (pool_malloc(&t, bytes, st) != cudaSuccess) return ROSKO_ERR_OOM;
   rosko_status s = transpose_impl(A_dev, a_dtype, M, K, lda, t, st);
   if (s == ROSKO_OK)
     s = rosko_pack(t, a_dtype, K, M, std::max<int64_t>(M, 1), packed_dtype, row_scale_dev, tile,
                    stream, out);
-  // the pack synchronised the stream: the scratch is no longer read
-  cudaStreamSynchronize(st);
-  cudaFree(t);
+  // stream-ordered: released after the pack's reads of the copy
+  pool_free(t, st);
   return s;
 }
 
 void rosko_free(rosko_packed_t A) {
   if (!A || A->magic != kHandleMagic) return;
   A->magic = 0;
-  if (A->meta_base) cudaFree(A->meta_base);
-  if (A->data_base) cudaFree(A->data_base);
-  if (A->dense_base) cudaFree(A->dense_base);
-  if (A->row_base) cudaFree(A->row_base);
-  if (A->gather_base) cudaFree(A->gather_base);
-  if (A->seg_base) cudaFree(A->seg_base);
+  if (A->base) {
+    // queued work on any stream may still read the handle: wait for the
+    // device, as cudaFree would, then hand the memory back to the pool
+    int cur = 0;
+    const bool other = cudaGetDevice(&cur) == cudaSuccess && cur != A->device;
+    if (other) cudaSetDevice(A->device);
+    cudaDeviceSynchronize();
+    pool_free(A->base, nullptr);
+    if (other) cudaSetDevice(cur);
+  }
   delete A;
 }
 

@@ -52,20 +52,17 @@ struct rosko_packed_s {
   int32_t m_r = 0;
   rosko_dtype dt = ROSKO_F32;
   int64_t nnz = 0, n_cols = 0, touched_k = 0;
-  void* meta_base = nullptr;  // panel_col, row_scale, features
-  void* data_base = nullptr;  // colrec, nz
+  void* base = nullptr;  // one device allocation holding every array below
   int32_t* panel_col = nullptr;
   int2* colrec = nullptr;
   void* nz = nullptr;
   float* row_scale = nullptr;
-  void* row_base = nullptr;     // rowptr, rnz
   int32_t* rowptr = nullptr;
   void* rnz = nullptr;
   // Touched-row gather stream (m_r = 16): per 128-row tile t the distinct
   // columns its rows touch (the tile's Alg. 1 col_ind), gu_k[gu_start[t] ..
   // gu_start[t+1]), and per row the records (value, slot) where slot is the
   // position of k in the tile's list (same rowptr as rnz).
-  void* gather_base = nullptr;
   int32_t* gu_start = nullptr;
   int32_t* gu_k = nullptr;
   void* gnz = nullptr;
@@ -86,7 +83,6 @@ struct rosko_packed_s {
     int32_t records = kSegRecords;
   };
   SegList segs[2];
-  void* seg_base = nullptr;
   float* feat_dev = nullptr;   // kNumFeatures floats (N-independent part)
   int64_t* panel_nnz_dev = nullptr;  // P+1 nonzero offsets of panels
   // Dense-panel split (BF16 only).  128-row tiles sorted by density,
@@ -95,7 +91,6 @@ struct rosko_packed_s {
   // the tiles in the reverse order (ascending density), so for any threshold
   // the sparse panels are a prefix of it.
   int64_t n_tiles = 0, n_copy = 0, Kpad = 0;
-  void* dense_base = nullptr;
   void* dense_A = nullptr;
   int32_t* tile_order_dev = nullptr;
   int32_t* panel_order_dev = nullptr;

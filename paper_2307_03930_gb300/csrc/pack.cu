@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "handle.hpp"
@@ -128,25 +129,6 @@ __global__ void rowscale_kernel(const float* __restrict__ A, int64_t M, int64_t 
   if (lane == 0) scale[row] = (m == 0.0f) ? 1.0f : __fdiv_rn(m, 127.0f);
 }
 
-// Pass 1: cnt[p*K + k] = (nonzeros of column k in panel p, 1 if non-empty).
-template <class S, class D>
-__global__ void count_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda, int m_r,
-                             const float* __restrict__ scale, int2* __restrict__ cnt,
-                             int* __restrict__ touched) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t p = blockIdx.y;
-  if (k >= K) return;
-  const int64_t m0 = p * m_r;
-  const int64_t m1 = min(M, m0 + m_r);
-  int c = 0;
-  for (int64_t m = m0; m < m1; ++m) {
-    D v;
-    c += Conv<S, D>::get(A[m * lda + k], scale ? scale[m] : 1.0f, v) ? 1 : 0;
-  }
-  cnt[p * K + k] = make_int2(c, c != 0);
-  if (c) touched[k] = 1;
-}
-
 __device__ __forceinline__ int2 add2(int2 a, int2 b) { return make_int2(a.x + b.x, a.y + b.y); }
 
 __device__ __forceinline__ int2 warp_incl_scan(int2 v) {
@@ -180,117 +162,86 @@ __device__ int2 block_excl_scan(int2 v, int2* total) {
   return make_int2(base.x + inc.x - v.x, base.y + inc.y - v.y);
 }
 
-// Scan pass A: per-tile sums.
-__global__ void scan_reduce_kernel(const int2* __restrict__ in, int64_t n, int2* __restrict__ sums) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  int2 s = make_int2(0, 0);
-  for (int i = 0; i < kScanItems; ++i) {
-    const int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
-    if (idx < n) s = add2(s, in[idx]);
-  }
-  int2 total;
-  block_excl_scan(s, &total);
-  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+// Up to three independent exclusive scans of int2 arrays in place, sharing
+// each of the three launches of a tiled scan: job i owns blocks
+// [first[i], first[i+1]) of the tile passes and block i of the spine pass.
+// data[n] receives the total; sums holds nb + 1 entries (nb = tiles of job).
+struct ScanJob {
+  int2* data;
+  int64_t n;
+  int2* sums;
+  int64_t nb;
+};
+struct ScanSet {
+  ScanJob job[3];
+  int64_t first[4];
+  int count;
+};
+
+__device__ __forceinline__ int scan_job_of(const ScanSet& s, int64_t b) {
+  int i = 0;
+  while (i + 1 < s.count && b >= s.first[i + 1]) ++i;
+  return i;
 }
 
-// Scan pass B: exclusive scan of the tile sums (one block, chunked), writes the
-// grand total to sums[nb].
-__global__ void scan_spine_kernel(int2* __restrict__ sums, int64_t nb) {
+// Tile pass A: per-tile sums.
+__global__ void scan_reduce_kernel(ScanSet s) {
+  const int j = scan_job_of(s, blockIdx.x);
+  const ScanJob J = s.job[j];
+  const int64_t base = ((int64_t)blockIdx.x - s.first[j]) * kScanTile;
+  int2 v = make_int2(0, 0);
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
+    if (idx < J.n) v = add2(v, J.data[idx]);
+  }
+  int2 total;
+  block_excl_scan(v, &total);
+  if (threadIdx.x == 0) J.sums[blockIdx.x - s.first[j]] = total;
+}
+
+// Spine pass B: exclusive scan of one job's tile sums (chunked), total to
+// sums[nb].
+__global__ void scan_spine_kernel(ScanSet s) {
+  const ScanJob J = s.job[blockIdx.x];
   int2 carry = make_int2(0, 0);
-  for (int64_t c0 = 0; c0 < nb; c0 += kScanThreads) {
+  for (int64_t c0 = 0; c0 < J.nb; c0 += kScanThreads) {
     const int64_t idx = c0 + threadIdx.x;
-    int2 v = idx < nb ? sums[idx] : make_int2(0, 0);
+    int2 v = idx < J.nb ? J.sums[idx] : make_int2(0, 0);
     int2 total;
     int2 ex = block_excl_scan(v, &total);
-    if (idx < nb) sums[idx] = add2(ex, carry);
+    if (idx < J.nb) J.sums[idx] = add2(ex, carry);
     carry = add2(carry, total);
     __syncthreads();
   }
-  if (threadIdx.x == 0) sums[nb] = carry;
+  if (threadIdx.x == 0) J.sums[J.nb] = carry;
 }
 
-// Scan pass C: in-place exclusive scan of each tile with its offset; the
-// element n receives the grand total.
-__global__ void scan_down_kernel(int2* __restrict__ data, int64_t n, const int2* __restrict__ sums,
-                                 int64_t nb) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+// Tile pass C: in-place exclusive scan of each tile with its offset.
+__global__ void scan_down_kernel(ScanSet s) {
+  const int j = scan_job_of(s, blockIdx.x);
+  const ScanJob J = s.job[j];
+  const int64_t tile = (int64_t)blockIdx.x - s.first[j];
+  const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int2 v[kScanItems];
-  int2 s = make_int2(0, 0);
+  int2 sum = make_int2(0, 0);
   for (int i = 0; i < kScanItems; ++i) {
-    v[i] = (base + i < n) ? data[base + i] : make_int2(0, 0);
-    s = add2(s, v[i]);
+    v[i] = (base + i < J.n) ? J.data[base + i] : make_int2(0, 0);
+    sum = add2(sum, v[i]);
   }
   int2 total;
-  int2 off = add2(block_excl_scan(s, &total), sums[blockIdx.x]);
+  int2 off = add2(block_excl_scan(sum, &total), J.sums[tile]);
   for (int i = 0; i < kScanItems; ++i) {
-    if (base + i < n) data[base + i] = off;
+    if (base + i < J.n) J.data[base + i] = off;
     off = add2(off, v[i]);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) data[n] = sums[nb];
-}
-
-__global__ void sum_flags_kernel(const int* __restrict__ f, int64_t n, int* __restrict__ out) {
-  int s = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    s += f[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
-}
-
-// Pass 3: column records and values.  off[p*K+k] = (first nonzero, first
-// packed column) of that panel column; the count is the difference with the
-// next entry.
-template <class S, class D>
-__global__ void scatter_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda, int m_r,
-                               const float* __restrict__ scale, const int2* __restrict__ off,
-                               int2* __restrict__ colrec, void* __restrict__ nz,
-                               int32_t* __restrict__ panel_col, int64_t* __restrict__ panel_nnz) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t p = blockIdx.y;
-  if (k >= K) return;
-  const int64_t pk = p * K + k;
-  const int2 o = off[pk];
-  if (k == 0) {
-    panel_col[p] = o.y;
-    panel_nnz[p] = o.x;
-  }
-  const int cnt = off[pk + 1].x - o.x;
-  if (cnt == 0) return;
-  colrec[o.y] = make_int2((int32_t)k, o.x);
-  const int64_t m0 = p * m_r;
-  const int64_t m1 = min(M, m0 + m_r);
-  int64_t e = o.x;
-  for (int64_t m = m0; m < m1; ++m) {
-    D v;
-    if (Conv<S, D>::get(A[m * lda + k], scale ? scale[m] : 1.0f, v)) {
-      put_rec(nz, e, v, (int)(m - m0));
-      ++e;
-    }
-  }
+  if (tile == 0 && threadIdx.x == 0) J.data[J.n] = J.sums[J.nb];
 }
 
 // Dense BF16 copies of 128-row tiles for the tensor-core dense-panel path:
-// row block c of `out` holds rows tile_order[c]*128 .. +127 of A (zero past M
-// and past K; row stride Kpad).  Values are converted exactly as the packer
-// converts them.
+// row block c holds rows tile_order[c]*128 .. +127 of A (zero past M and past
+// K; row stride Kpad), converted exactly as the packer converts them.
 __device__ __forceinline__ __nv_bfloat16 to_bf16(float a) { return __float2bfloat16_rn(a); }
 __device__ __forceinline__ __nv_bfloat16 to_bf16(__nv_bfloat16 a) { return a; }
-
-template <class S>
-__global__ void densify_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
-                               const int32_t* __restrict__ tile_order, int64_t n_rows,
-                               int64_t Kpad, __nv_bfloat16* __restrict__ out) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= Kpad) return;
-  for (int64_t rr = blockIdx.y; rr < n_rows; rr += gridDim.y) {
-    const int64_t row = (int64_t)tile_order[rr / kDenseTileRows] * kDenseTileRows +
-                        rr % kDenseTileRows;
-    __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-    if (row < M && k < K) v = to_bf16(A[row * lda + k]);
-    out[rr * Kpad + k] = v;
-  }
-}
 
 // Row-slot stream records (value + column k) and the per-row sentinel.
 __device__ __forceinline__ void put_row_rec(void* rnz, int64_t e, float v, int k) {
@@ -324,69 +275,67 @@ __device__ __forceinline__ void put_row_sentinel(void* rnz, int64_t e) {
   }
 }
 
-// Row-slot pass 1: cnt[row] = (nonzeros of the row + 1 sentinel, 0); one warp
-// per row, lanes over consecutive columns (coalesced).
+// ----------------------------------------------------------------------------
+// The passes of one phase share a launch: a 1-D grid of 256-thread blocks in
+// consecutive ranges, one range per pass (a block runs exactly one pass).
+constexpr int kPackThreads = 256;
+constexpr int kRowsPerBlock = kPackThreads / 32;   // row passes: one warp per row
+
+struct PackGeom {
+  int64_t M, K, lda, P, T;
+  int m_r;
+  int64_t gx;   // 256-column groups, ceil(K / 256)
+};
+
+// Counting pass, Alg. 1's per-column nnz: cnt[p*K + k] = (nonzeros of column
+// k in panel p, 1 if non-empty); a column's first nonzero seen anywhere
+// counts it as touched.
 template <class S, class D>
-__global__ void row_count_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
-                                 const float* __restrict__ scale, int2* __restrict__ cnt) {
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+__device__ void col_count(const S* __restrict__ A, const PackGeom& g,
+                          const float* __restrict__ scale, int64_t b, int2* __restrict__ cnt,
+                          int* __restrict__ touched, int* __restrict__ touched_total) {
+  const int64_t k = (b % g.gx) * kPackThreads + threadIdx.x;
+  const int64_t p = b / g.gx;
+  if (k >= g.K) return;
+  const int64_t m0 = p * g.m_r, m1 = min(g.M, m0 + g.m_r);
+  int c = 0;
+#pragma unroll 8
+  for (int64_t m = m0; m < m1; ++m) {
+    D v;
+    c += Conv<S, D>::get(A[m * g.lda + k], scale ? scale[m] : 1.0f, v) ? 1 : 0;
+  }
+  cnt[p * g.K + k] = make_int2(c, c != 0);
+  if (c && atomicExch(&touched[k], 1) == 0) atomicAdd(touched_total, 1);
+}
+
+// Counting pass of the row-slot stream: rcnt[row] = (nonzeros of the row + 1
+// sentinel, 0); lanes over consecutive columns (coalesced).
+template <class S, class D>
+__device__ void row_count(const S* __restrict__ A, const PackGeom& g,
+                          const float* __restrict__ scale, int64_t b, int2* __restrict__ rcnt) {
+  const int64_t row = b * kRowsPerBlock + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
-  if (row >= M) return;
+  if (row >= g.M) return;
   const float sc = scale ? scale[row] : 1.0f;
   int c = 0;
 #pragma unroll 8
-  for (int64_t k = lane; k < K; k += 32) {
+  for (int64_t k = lane; k < g.K; k += 32) {
     D v;
-    c += Conv<S, D>::get(A[row * lda + k], sc, v) ? 1 : 0;
+    c += Conv<S, D>::get(A[row * g.lda + k], sc, v) ? 1 : 0;
   }
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if (lane == 0) cnt[row] = make_int2(c + 1, 0);
+  if (lane == 0) rcnt[row] = make_int2(c + 1, 0);
 }
 
-// Row-slot pass 2: write each row's records (k ascending) at the scanned
-// offset, then its sentinel.
+// Counting pass of the gather stream: flag[t*K + k] = (1 if any row of
+// 128-row tile t has a nonzero in column k, 0).
 template <class S, class D>
-__global__ void row_write_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
-                                 const float* __restrict__ scale, const int2* __restrict__ off,
-                                 int32_t* __restrict__ rowptr, void* __restrict__ rnz) {
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (row >= M) return;
-  const float sc = scale ? scale[row] : 1.0f;
-  int64_t pos = off[row].x;
-  if (lane == 0) rowptr[row] = (int32_t)pos;
-  // eight 32-column groups per step: their loads are issued together, then
-  // the records are written in k order
-  constexpr int G = 8;
-  for (int64_t k0 = 0; k0 < K; k0 += 32 * G) {
-    S a[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int64_t k = k0 + g * 32 + lane;
-      a[g] = k < K ? A[row * lda + k] : S(0);
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int64_t k = k0 + g * 32 + lane;
-      D v;
-      const bool nzf = (k < K) && Conv<S, D>::get(a[g], sc, v);
-      const unsigned mask = __ballot_sync(0xffffffffu, nzf);
-      if (nzf) put_row_rec(rnz, pos + __popc(mask & ((1u << lane) - 1u)), v, (int)k);
-      pos += __popc(mask);
-    }
-  }
-  if (lane == 0) put_row_sentinel<D>(rnz, pos);
-}
-
-// Gather stream, pass 1: flag[t*K + k] = (1 if any row of 128-row tile t has a
-// nonzero in column k, 0).
-template <class S, class D>
-__global__ void tile_flag_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
-                                 const float* __restrict__ scale, int2* __restrict__ flag) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t t = blockIdx.y;
-  if (k >= K) return;
-  const int64_t m0 = t * kDenseTileRows, m1 = min(M, m0 + kDenseTileRows);
+__device__ void tile_flag(const S* __restrict__ A, const PackGeom& g,
+                          const float* __restrict__ scale, int64_t b, int2* __restrict__ flag) {
+  const int64_t k = (b % g.gx) * kPackThreads + threadIdx.x;
+  const int64_t t = b / g.gx;
+  if (k >= g.K) return;
+  const int64_t m0 = t * kDenseTileRows, m1 = min(g.M, m0 + kDenseTileRows);
   int any = 0;
   // sixteen rows per step, loads issued together (no early exit, which would
   // serialise them)
@@ -395,53 +344,204 @@ __global__ void tile_flag_kernel(const S* __restrict__ A, int64_t M, int64_t K, 
     for (int u = 0; u < 16; ++u) {
       if (m + u < m1) {
         D v;
-        any |= Conv<S, D>::get(A[(m + u) * lda + k], scale ? scale[m + u] : 1.0f, v) ? 1 : 0;
+        any |= Conv<S, D>::get(A[(m + u) * g.lda + k], scale ? scale[m + u] : 1.0f, v) ? 1 : 0;
       }
     }
   }
-  flag[t * K + k] = make_int2(any, 0);
+  flag[t * g.K + k] = make_int2(any, 0);
 }
 
-// Gather stream, pass 2: the union lists gu_k and their per-tile offsets from
-// the scanned flags.
-__global__ void tile_union_kernel(const int2* __restrict__ off, int64_t K, int64_t T,
-                                  int32_t* __restrict__ gu_start, int32_t* __restrict__ gu_k) {
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t t = blockIdx.y;
-  if (k >= K) return;
-  const int64_t i = t * K + k;
-  if (k == 0) gu_start[t] = off[i].x;
-  if (off[i + 1].x != off[i].x) gu_k[off[i].x] = (int32_t)k;
+// Phase 1 in one launch: blocks [0, b_col) count panel columns, the next
+// b_row blocks count rows, the rest flag tile columns.
+template <class S, class D>
+__global__ void __launch_bounds__(kPackThreads)
+    pack_count_kernel(const S* __restrict__ A, PackGeom g, const float* __restrict__ scale,
+                      int2* __restrict__ cnt, int* __restrict__ touched,
+                      int* __restrict__ touched_total, int2* __restrict__ rcnt,
+                      int2* __restrict__ flag, int64_t b_col, int64_t b_row) {
+  int64_t b = blockIdx.x;
+  if (b < b_col) {
+    col_count<S, D>(A, g, scale, b, cnt, touched, touched_total);
+    return;
+  }
+  b -= b_col;
+  if (b < b_row) {
+    row_count<S, D>(A, g, scale, b, rcnt);
+    return;
+  }
+  tile_flag<S, D>(A, g, scale, b - b_row, flag);
 }
 
-// Gather stream, pass 3: each row-slot record re-addressed by its slot in the
-// tile's union list (same positions as the row-slot stream).
-template <class D>
-__global__ void gather_records_kernel(const int32_t* __restrict__ rowptr, const void* __restrict__ rnz,
-                                      const int2* __restrict__ off, int64_t M, int64_t K,
-                                      void* __restrict__ gnz) {
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (row >= M) return;
-  const int64_t t = row / kDenseTileRows;
-  const int32_t base = off[t * K].x;
-  const int32_t e0 = rowptr[row], e1 = rowptr[row + 1];   // last entry: sentinel
-  for (int32_t e = e0 + lane; e < e1; e += 32) {
-    if constexpr (sizeof(D) <= 2) {
-      const uint32_t w = reinterpret_cast<const uint32_t*>(rnz)[e];
-      const uint32_t k = w & 0xFFFFu;
-      const uint32_t slot = (e == e1 - 1) ? 0xFFFFu : (uint32_t)(off[t * K + k].x - base);
-      reinterpret_cast<uint32_t*>(gnz)[e] = (w & 0xFFFF0000u) | slot;
-    } else if constexpr (sizeof(D) == 4) {
-      uint2 w = reinterpret_cast<const uint2*>(rnz)[e];
-      if (e != e1 - 1) w.x = (uint32_t)(off[t * K + w.x].x - base);
-      reinterpret_cast<uint2*>(gnz)[e] = w;
-    } else {
-      RecF64 w = reinterpret_cast<const RecF64*>(rnz)[e];
-      if (e != e1 - 1) w.r = off[t * K + w.r].x - base;
-      reinterpret_cast<RecF64*>(gnz)[e] = w;
+// Pointers and block ranges of the writing phase.  Scanned offsets:
+// cnt[p*K+k] = (first nonzero, first packed column) of a panel column,
+// rcnt[row].x = first record of a row, flag[t*K+k].x = slot of column k in
+// tile t's union list (plus the tile's base).
+struct WriteArgs {
+  const int2* cnt;
+  int2* colrec;
+  void* nz;
+  int32_t* panel_col;
+  int64_t* panel_nnz;
+  const int2* rcnt;
+  int32_t* rowptr;
+  void* rnz;
+  const int2* flag;
+  int32_t* gu_start;
+  int32_t* gu_k;
+  void* gnz;
+  const int32_t* tile_order;
+  __nv_bfloat16* dense_A;
+  int64_t dense_rows, Kpad, gxd, ry;
+  int64_t nnz, n_cols, gu_total;
+  int zero_panels;
+  int64_t b_scatter, b_row, b_union, b_dense;
+};
+
+// Alg. 1's append: each non-empty panel column writes its column record and
+// its values with rows ascending at the scanned offsets.
+template <class S, class D>
+__device__ void scatter(const S* __restrict__ A, const PackGeom& g,
+                        const float* __restrict__ scale, int64_t b, const WriteArgs& w) {
+  const int64_t k = (b % g.gx) * kPackThreads + threadIdx.x;
+  const int64_t p = b / g.gx;
+  if (k >= g.K) return;
+  const int64_t pk = p * g.K + k;
+  const int2 o = w.cnt[pk];
+  if (k == 0) {
+    w.panel_col[p] = o.y;
+    w.panel_nnz[p] = o.x;
+  }
+  const int cnt = w.cnt[pk + 1].x - o.x;
+  if (cnt == 0) return;
+  w.colrec[o.y] = make_int2((int32_t)k, o.x);
+  const int64_t m0 = p * g.m_r, m1 = min(g.M, m0 + g.m_r);
+  int64_t e = o.x;
+  for (int64_t m = m0; m < m1; ++m) {
+    D v;
+    if (Conv<S, D>::get(A[m * g.lda + k], scale ? scale[m] : 1.0f, v)) {
+      put_rec(w.nz, e, v, (int)(m - m0));
+      ++e;
     }
   }
+}
+
+// Row-slot stream: each row's records (k ascending) at its scanned offset,
+// then its sentinel; with the gather stream, the same record re-addressed by
+// the slot of k in the tile's union list goes to the same position of gnz.
+template <class S, class D>
+__device__ void row_write(const S* __restrict__ A, const PackGeom& g,
+                          const float* __restrict__ scale, int64_t b, const WriteArgs& w) {
+  const int64_t row = b * kRowsPerBlock + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= g.M) return;
+  const float sc = scale ? scale[row] : 1.0f;
+  int64_t pos = w.rcnt[row].x;
+  if (lane == 0) w.rowptr[row] = (int32_t)pos;
+  const int2* tf = w.flag ? w.flag + (row / kDenseTileRows) * g.K : nullptr;
+  const int32_t base = tf ? tf[0].x : 0;
+  // eight 32-column groups per step: their loads are issued together, then
+  // the records are written in k order
+  constexpr int G = 8;
+  for (int64_t k0 = 0; k0 < g.K; k0 += 32 * G) {
+    S a[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int64_t k = k0 + u * 32 + lane;
+      a[u] = k < g.K ? A[row * g.lda + k] : S(0);
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int64_t k = k0 + u * 32 + lane;
+      D v;
+      const bool nzf = (k < g.K) && Conv<S, D>::get(a[u], sc, v);
+      const unsigned mask = __ballot_sync(0xffffffffu, nzf);
+      if (nzf) {
+        const int64_t q = pos + __popc(mask & ((1u << lane) - 1u));
+        put_row_rec(w.rnz, q, v, (int)k);
+        if (tf) put_row_rec(w.gnz, q, v, (int)(tf[k].x - base));
+      }
+      pos += __popc(mask);
+    }
+  }
+  if (lane == 0) {
+    put_row_sentinel<D>(w.rnz, pos);
+    if (tf) put_row_sentinel<D>(w.gnz, pos);
+  }
+}
+
+// Gather stream: the union list gu_k of each tile and its offset gu_start.
+__device__ void tile_union(const PackGeom& g, int64_t b, const WriteArgs& w) {
+  const int64_t k = (b % g.gx) * kPackThreads + threadIdx.x;
+  const int64_t t = b / g.gx;
+  if (k >= g.K) return;
+  const int64_t i = t * g.K + k;
+  if (k == 0) w.gu_start[t] = w.flag[i].x;
+  if (w.flag[i + 1].x != w.flag[i].x) w.gu_k[w.flag[i].x] = (int32_t)k;
+}
+
+template <class S>
+__device__ void densify(const S* __restrict__ A, const PackGeom& g, int64_t b,
+                        const WriteArgs& w) {
+  const int64_t k = (b % w.gxd) * kPackThreads + threadIdx.x;
+  if (k >= w.Kpad) return;
+  for (int64_t rr = b / w.gxd; rr < w.dense_rows; rr += w.ry) {
+    const int64_t row = (int64_t)w.tile_order[rr / kDenseTileRows] * kDenseTileRows +
+                        rr % kDenseTileRows;
+    __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+    if (row < g.M && k < g.K) v = to_bf16(A[row * g.lda + k]);
+    w.dense_A[rr * w.Kpad + k] = v;
+  }
+}
+
+// Terminating entries: panel_col[P] = packed columns, panel_nnz[P] = nnz,
+// colrec[n_cols] = colrec[n_cols + 1] = {INT32_MAX, nnz}, rowptr[M] = nnz + M
+// (row stream), gu_start[T] = union total (gather stream); with no scatter
+// (K = 0) every panel starts at 0.
+__device__ void tails(const PackGeom& g, const WriteArgs& w) {
+  if (w.zero_panels)
+    for (int64_t p = threadIdx.x; p < g.P; p += blockDim.x) {
+      w.panel_col[p] = 0;
+      w.panel_nnz[p] = 0;
+    }
+  if (threadIdx.x == 0) {
+    w.panel_col[g.P] = (int32_t)w.n_cols;
+    w.panel_nnz[g.P] = w.nnz;
+    w.colrec[w.n_cols] = make_int2(INT32_MAX, (int32_t)w.nnz);
+    w.colrec[w.n_cols + 1] = make_int2(INT32_MAX, (int32_t)w.nnz);
+    if (w.rowptr) w.rowptr[g.M] = (int32_t)(w.nnz + g.M);
+    if (w.gu_start) w.gu_start[g.T] = (int32_t)w.gu_total;
+  }
+}
+
+// Phase 2 in one launch: scatter, row write (+ gather records), union lists,
+// dense copies, then one block of terminating entries.
+template <class S, class D>
+__global__ void __launch_bounds__(kPackThreads)
+    pack_write_kernel(const S* __restrict__ A, PackGeom g, const float* __restrict__ scale,
+                      WriteArgs w) {
+  int64_t b = blockIdx.x;
+  if (b < w.b_scatter) {
+    scatter<S, D>(A, g, scale, b, w);
+    return;
+  }
+  b -= w.b_scatter;
+  if (b < w.b_row) {
+    row_write<S, D>(A, g, scale, b, w);
+    return;
+  }
+  b -= w.b_row;
+  if (b < w.b_union) {
+    tile_union(g, b, w);
+    return;
+  }
+  b -= w.b_union;
+  if constexpr (std::is_same<D, __nv_bfloat16>::value) {
+    if (b < w.b_dense) {
+      densify<S>(A, g, b, w);
+      return;
+    }
+  }
+  tails(g, w);
 }
 
 template <class D>
@@ -465,223 +565,46 @@ struct Scratch {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <class S, class D>
-rosko_status build_row_stream(const S* A, int64_t lda, const float* scale, rosko_packed_s* h,
-                              cudaStream_t st);
+// Stream-ordered scratch from the library's pool, released in the order of
+// its stream (so an early return never frees memory that queued work uses).
+struct PoolScratch {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  ~PoolScratch() { pool_free(p, st); }
+};
 
-template <class S, class D>
-rosko_status pack_typed(const S* A, int64_t M, int64_t K, int64_t lda, const float* scale_in,
-                        bool quantize_rows, rosko_packed_s* h, cudaStream_t st) {
-  const int64_t P = h->P;
-  const int64_t n = P * K;
-  const int64_t nb = (n + kScanTile - 1) / kScanTile;
-  // scratch: cnt/off (n+1 int2), tile sums (nb+1 int2), touched flags (K int),
-  // three ints of totals
-  const size_t off_cnt = 0;
-  const size_t off_sums = align_up(off_cnt + (size_t)(n + 1) * sizeof(int2), 256);
-  const size_t off_touch = align_up(off_sums + (size_t)(nb + 1) * sizeof(int2), 256);
-  const size_t off_tot = align_up(off_touch + (size_t)K * sizeof(int), 256);
-  const size_t scratch_bytes = off_tot + 256;
-  Scratch scr;
-  if (dev_malloc(&scr.p, scratch_bytes) != cudaSuccess) return ROSKO_ERR_OOM;
-  char* sb = static_cast<char*>(scr.p);
-  int2* cnt = reinterpret_cast<int2*>(sb + off_cnt);
-  int2* sums = reinterpret_cast<int2*>(sb + off_sums);
-  int* touched = reinterpret_cast<int*>(sb + off_touch);
-  int* tot = reinterpret_cast<int*>(sb + off_tot);
-
-  // meta allocation: panel_col (P+1 int32), panel_nnz (P+1 int64), row_scale (M),
-  // features
-  const size_t m_pc = 0;
-  const size_t m_pn = align_up(m_pc + (size_t)(P + 1) * 4, 256);
-  const size_t m_rs = align_up(m_pn + (size_t)(P + 1) * 8, 256);
-  const size_t m_ft = align_up(m_rs + (size_t)std::max<int64_t>(M, 1) * 4, 256);
-  const size_t meta_bytes = m_ft + 256;
-  if (dev_malloc(&h->meta_base, meta_bytes) != cudaSuccess) return ROSKO_ERR_OOM;
-  char* mb = static_cast<char*>(h->meta_base);
-  h->panel_col = reinterpret_cast<int32_t*>(mb + m_pc);
-  h->panel_nnz_dev = reinterpret_cast<int64_t*>(mb + m_pn);
-  h->row_scale = reinterpret_cast<float*>(mb + m_rs);
-  h->feat_dev = reinterpret_cast<float*>(mb + m_ft);
-
-  if (cudaMemsetAsync(touched, 0, (size_t)K * sizeof(int) + 0, st) != cudaSuccess ||
-      cudaMemsetAsync(tot, 0, 16, st) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-
-  const float* scale = nullptr;
-  if (quantize_rows) {
-    const int wpb = 8;
-    if (M > 0)
-      rowscale_kernel<<<(unsigned)((M + wpb - 1) / wpb), wpb * 32, 0, st>>>(
-          reinterpret_cast<const float*>(A), M, K, lda, h->row_scale);
-    if (M > 0) count_launches(1);
-    scale = h->row_scale;
-  } else if (h->dt == ROSKO_I8) {
-    if (scale_in) {
-      if (cudaMemcpyAsync(h->row_scale, scale_in, (size_t)M * 4, cudaMemcpyDeviceToDevice, st) !=
-          cudaSuccess)
-        return ROSKO_ERR_CUDA;
-    } else {
-      // all-ones scales: write with a trivial fill through memset of 0x3f800000
-      // is not byte-uniform, so use a host copy of ones
-      float* ones = new (std::nothrow) float[M > 0 ? M : 1];
-      if (!ones) return ROSKO_ERR_OOM;
-      for (int64_t i = 0; i < M; ++i) ones[i] = 1.0f;
-      cudaError_t e = cudaMemcpyAsync(h->row_scale, ones, (size_t)M * 4, cudaMemcpyHostToDevice, st);
-      cudaError_t e2 = cudaStreamSynchronize(st);
-      delete[] ones;
-      if (e != cudaSuccess || e2 != cudaSuccess) return ROSKO_ERR_CUDA;
-    }
-  }
-
-  const int T = 256;
-  const dim3 grid((unsigned)((K + T - 1) / T), (unsigned)P);
-  if (n > 0) {
-    count_kernel<S, D><<<grid, T, 0, st>>>(A, M, K, lda, h->m_r, scale, cnt, touched);
-    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(cnt, n, sums);
-    scan_spine_kernel<<<1, kScanThreads, 0, st>>>(sums, nb);
-    scan_down_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(cnt, n, sums, nb);
-    sum_flags_kernel<<<std::min<int64_t>((K + 255) / 256, 1024), 256, 0, st>>>(touched, K, tot + 2);
-    count_launches(5);
-  } else {
-    if (cudaMemsetAsync(cnt, 0, sizeof(int2), st) != cudaSuccess) return ROSKO_ERR_CUDA;
-  }
-  if (cudaGetLastError() != cudaSuccess) return ROSKO_ERR_CUDA;
-  int host_tot[4] = {0, 0, 0, 0};
-  if (cudaMemcpyAsync(host_tot, cnt + n, sizeof(int2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(host_tot + 2, tot + 2, sizeof(int), cudaMemcpyDeviceToHost, st) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  h->nnz = host_tot[0];
-  h->n_cols = host_tot[1];
-  h->touched_k = host_tot[2];
-
-  const size_t rsz = rec_size(h->dt);
-  const size_t d_cr = 0;
-  const size_t d_nz = align_up(d_cr + (size_t)(h->n_cols + 2) * 8, 256);
-  const size_t data_bytes = d_nz + (size_t)(h->nnz + 1) * rsz + 256;
-  if (dev_malloc(&h->data_base, data_bytes) != cudaSuccess) return ROSKO_ERR_OOM;
-  char* db = static_cast<char*>(h->data_base);
-  h->colrec = reinterpret_cast<int2*>(db + d_cr);
-  h->nz = db + d_nz;
-
-  if (n > 0)
-    scatter_kernel<S, D><<<grid, T, 0, st>>>(A, M, K, lda, h->m_r, scale, cnt, h->colrec, h->nz,
-                                             h->panel_col, h->panel_nnz_dev);
-  if (n > 0) count_launches(1);
-  // tails: panel_col[P] = n_cols, panel_nnz[P] = nnz, colrec[n_cols] = {INT32_MAX, nnz}
-  int32_t tail32[1] = {(int32_t)h->n_cols};
-  int2 tailrec[2] = {make_int2(INT32_MAX, (int32_t)h->nnz), make_int2(INT32_MAX, (int32_t)h->nnz)};
-  int64_t tail64 = h->nnz;
-  if (cudaMemcpyAsync(h->panel_col + P, &tail32[0], 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(h->colrec + h->n_cols, tailrec, sizeof(tailrec), cudaMemcpyHostToDevice,
-                      st) != cudaSuccess ||
-      cudaMemcpyAsync(h->panel_nnz_dev + P, &tail64, 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  if (P == 0 || K == 0) {
-    // no scatter ran: every panel starts at 0
-    if (P > 0 && (cudaMemsetAsync(h->panel_col, 0, (size_t)P * 4, st) != cudaSuccess ||
-                  cudaMemsetAsync(h->panel_nnz_dev, 0, (size_t)P * 8, st) != cudaSuccess))
-      return ROSKO_ERR_CUDA;
-  }
-  // the scratch and the host tails above must outlive the queued work
-  if (cudaStreamSynchronize(st) != cudaSuccess) return ROSKO_ERR_CUDA;
-  if (cudaGetLastError() != cudaSuccess) return ROSKO_ERR_CUDA;
-  return build_row_stream<S, D>(A, lda, scale, h, st);
+__global__ void fill_kernel(float* __restrict__ out, int64_t n, float v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = v;
 }
 
-// Exclusive scan of n int2 in place (data[n] receives the total); `sums`
-// holds at least (n + kScanTile - 1) / kScanTile + 1 entries.
-void run_scan(int2* data, int64_t n, int2* sums, cudaStream_t st) {
-  const int64_t nb = (n + kScanTile - 1) / kScanTile;
-  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, sums);
-  scan_spine_kernel<<<1, kScanThreads, 0, st>>>(sums, nb);
-  scan_down_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(data, n, sums, nb);
-  count_launches(3);
+// What the host needs to lay out the handle, gathered from the scans into one
+// array so that a single copy brings it back:
+//   sum64[0..3]    nonzeros, packed columns, touched columns, gather-union total
+//   sum64[4..4+P]  nonzero offset of every panel, then the total
+//   rowptr[0..M]   row-stream offsets (row stream only)
+__global__ void pack_summary_kernel(const int2* __restrict__ cnt, int64_t n, int64_t P, int64_t K,
+                                    const int* __restrict__ touched_total,
+                                    const int2* __restrict__ rcnt, int64_t M,
+                                    const int2* __restrict__ flag, int64_t nf,
+                                    int64_t* __restrict__ sum64, int32_t* __restrict__ rowptr) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    sum64[0] = cnt[n].x;
+    sum64[1] = cnt[n].y;
+    sum64[2] = *touched_total;
+    sum64[3] = flag ? flag[nf].x : 0;
+  }
+  if (i <= P) sum64[4 + i] = i < P ? cnt[i * K].x : cnt[n].x;
+  if (rcnt && i <= M) rowptr[i] = rcnt[i].x;
 }
 
-// Row-slot execution stream: the same nonzeros ordered by (row, k), one
-// sentinel per row.  Needs K < kRowSlotMaxK (16-bit k in 32-bit records).
-template <class S, class D>
-rosko_status build_row_stream(const S* A, int64_t lda, const float* scale, rosko_packed_s* h,
-                              cudaStream_t st) {
-  const int64_t M = h->M, K = h->K;
-  if (M == 0 || K >= kRowSlotMaxK) return ROSKO_OK;
-  const int64_t nb = (M + kScanTile - 1) / kScanTile;
-  Scratch scr;
-  const size_t o_sum = align_up((size_t)(M + 1) * sizeof(int2), 256);
-  if (dev_malloc(&scr.p, o_sum + (size_t)(nb + 1) * sizeof(int2)) != cudaSuccess)
-    return ROSKO_ERR_OOM;
-  int2* cnt = static_cast<int2*>(scr.p);
-  int2* sums = reinterpret_cast<int2*>(static_cast<char*>(scr.p) + o_sum);
-  const size_t rsz = rec_size(h->dt);
-  const size_t o_rnz = align_up((size_t)(M + 1) * 4, 256);
-  const size_t bytes = o_rnz + (size_t)(h->nnz + M) * rsz + 256;
-  if (dev_malloc(&h->row_base, bytes) != cudaSuccess) return ROSKO_ERR_OOM;
-  h->rowptr = static_cast<int32_t*>(h->row_base);
-  h->rnz = static_cast<char*>(h->row_base) + o_rnz;
-  const int wpb = 8;
-  const unsigned blocks = (unsigned)((M + wpb - 1) / wpb);
-  row_count_kernel<S, D><<<blocks, wpb * 32, 0, st>>>(A, M, K, lda, scale, cnt);
-  count_launches(1);
-  run_scan(cnt, M, sums, st);
-  row_write_kernel<S, D><<<blocks, wpb * 32, 0, st>>>(A, M, K, lda, scale, cnt, h->rowptr,
-                                                      h->rnz);
-  count_launches(1);
-  const int32_t tail = (int32_t)(h->nnz + M);
-  if (cudaMemcpyAsync(h->rowptr + M, &tail, 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  if (h->m_r != 16 || K == 0) return ROSKO_OK;
-
-  // touched-row gather stream: per 128-row tile, the union of its columns
-  const int64_t T = (M + kDenseTileRows - 1) / kDenseTileRows;
-  const int64_t n = T * K;
-  const int64_t nbt = (n + kScanTile - 1) / kScanTile;
-  Scratch fs;
-  const size_t f_sum = align_up((size_t)(n + 1) * sizeof(int2), 256);
-  if (dev_malloc(&fs.p, f_sum + (size_t)(nbt + 1) * sizeof(int2)) != cudaSuccess)
-    return ROSKO_ERR_OOM;
-  int2* flag = static_cast<int2*>(fs.p);
-  int2* fsums = reinterpret_cast<int2*>(static_cast<char*>(fs.p) + f_sum);
-  const dim3 g2((unsigned)((K + 255) / 256), (unsigned)T);
-  tile_flag_kernel<S, D><<<g2, 256, 0, st>>>(A, M, K, lda, scale, flag);
-  count_launches(1);
-  run_scan(flag, n, fsums, st);
-  int2 tot;
-  if (cudaMemcpyAsync(&tot, flag + n, sizeof(int2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  h->gu_total = tot.x;
-  const size_t o_k = align_up((size_t)(T + 1) * 4, 256);
-  const size_t o_g = align_up(o_k + (size_t)std::max<int64_t>(tot.x, 1) * 4, 256);
-  if (dev_malloc(&h->gather_base, o_g + (size_t)(h->nnz + M) * rsz + 256) != cudaSuccess)
-    return ROSKO_ERR_OOM;
-  char* gb = static_cast<char*>(h->gather_base);
-  h->gu_start = reinterpret_cast<int32_t*>(gb);
-  h->gu_k = reinterpret_cast<int32_t*>(gb + o_k);
-  h->gnz = gb + o_g;
-  tile_union_kernel<<<g2, 256, 0, st>>>(flag, K, T, h->gu_start, h->gu_k);
-  gather_records_kernel<D><<<blocks, wpb * 32, 0, st>>>(h->rowptr, h->rnz, flag, M, K, h->gnz);
-  count_launches(2);
-  const int32_t gtail = tot.x;
-  if (cudaMemcpyAsync(h->gu_start + T, &gtail, 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  return ROSKO_OK;
-}
-
-// Dense-panel split bookkeeping and dense copies (BF16 packs only).
-template <class S>
-rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pm, rosko_packed_s* h,
-                               cudaStream_t st) {
+// Dense-panel split bookkeeping (BF16 packs): 128-row tiles sorted by density,
+// descending; the tiles at or above dense_min_pm per mille get a dense copy;
+// panel_order lists the panels tile by tile in ascending density.
+void plan_dense_tiles(rosko_packed_s* h, int32_t dense_min_pm) {
   const int64_t M = h->M, K = h->K, P = h->P;
-  if (M == 0 || K == 0) return ROSKO_OK;
-  h->panel_nnz.assign((size_t)P + 1, 0);
-  if (cudaMemcpy(h->panel_nnz.data(), h->panel_nnz_dev, (size_t)(P + 1) * 8,
-                 cudaMemcpyDeviceToHost) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
   const int64_t T = (M + kDenseTileRows - 1) / kDenseTileRows;
   const int64_t ppt = kDenseTileRows / h->m_r;
   std::vector<double> dens((size_t)T);
@@ -714,45 +637,15 @@ rosko_status build_dense_tiles(const S* A, int64_t lda, int32_t dense_min_pm, ro
   h->n_tiles = T;
   h->n_copy = n_copy;
   h->Kpad = (K + 7) / 8 * 8;
-  const size_t o_to = 0;
-  const size_t o_po = align_up(o_to + (size_t)T * 4, 256);
-  const size_t o_da = align_up(o_po + (size_t)P * 4, 1024);
-  const size_t bytes = o_da + (size_t)n_copy * kDenseTileRows * (size_t)h->Kpad * 2 + 256;
-  if (dev_malloc(&h->dense_base, bytes) != cudaSuccess) return ROSKO_ERR_OOM;
-  char* b = static_cast<char*>(h->dense_base);
-  h->tile_order_dev = reinterpret_cast<int32_t*>(b + o_to);
-  h->panel_order_dev = reinterpret_cast<int32_t*>(b + o_po);
-  h->dense_A = b + o_da;
-  if (cudaMemcpyAsync(h->tile_order_dev, h->tile_order.data(), (size_t)T * 4,
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(h->panel_order_dev, panel_order.data(), (size_t)P * 4,
-                      cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  if (n_copy > 0) {
-    const int64_t rows = n_copy * kDenseTileRows;
-    const dim3 grid((unsigned)((h->Kpad + 255) / 256), (unsigned)std::min<int64_t>(rows, 65535));
-    densify_kernel<S><<<grid, 256, 0, st>>>(A, M, K, lda, h->tile_order_dev, rows, h->Kpad,
-                                            reinterpret_cast<__nv_bfloat16*>(h->dense_A));
-    count_launches(1);
-  }
-  // host vectors are staged by the copies above; wait before they go away
-  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  return ROSKO_OK;
 }
 
-// Row-direct work segments (see rosko_packed_s): built on the host from the
-// row pointers, once per pack, at both granularities.
-rosko_status build_segments(rosko_packed_s* h, const std::vector<int32_t>* panel_order,
-                            cudaStream_t st) {
+// Row-direct work segments (see rosko_packed_s) from the row-stream offsets,
+// at both granularities: {row, piece} in row order (nat) and, with a panel
+// order, in that order (ord).
+void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32_t>* panel_order,
+                   std::vector<int2> nat[2], std::vector<int2> ord[2]) {
   const int64_t M = h->M, P = h->P;
-  if (!h->rowptr || M == 0) return ROSKO_OK;
-  std::vector<int32_t> rp((size_t)M + 1);
-  if (cudaStreamSynchronize(st) != cudaSuccess ||
-      cudaMemcpy(rp.data(), h->rowptr, (size_t)(M + 1) * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
   const int64_t lens[2] = {kSegRecords, seg_records_for(h->nnz, M)};
-  std::vector<int2> nat[2], ord[2];
   for (int g = 0; g < 2; ++g) {
     const int64_t seg = lens[g];
     rosko_packed_s::SegList& L = h->segs[g];
@@ -763,7 +656,7 @@ rosko_status build_segments(rosko_packed_s* h, const std::vector<int32_t>* panel
     for (int64_t p = 0; p < P; ++p) {
       panel_seg[(size_t)p] = (int64_t)nat[g].size();
       for (int64_t r = p * h->m_r; r < std::min<int64_t>(M, (p + 1) * h->m_r); ++r) {
-        const int64_t nr = (int64_t)rp[(size_t)r + 1] - rp[(size_t)r] - 1;   // minus the sentinel
+        const int64_t nr = (int64_t)rp[r + 1] - rp[r] - 1;   // minus the sentinel
         const int64_t ns = std::max<int64_t>(1, (nr + seg - 1) / seg);
         if (ns > 1) panel_split[(size_t)p] = 1;
         for (int64_t k = 0; k < ns; ++k) nat[g].push_back(make_int2((int)r, (int)k));
@@ -781,27 +674,267 @@ rosko_status build_segments(rosko_packed_s* h, const std::vector<int32_t>* panel
       L.split[(size_t)i + 1] = L.split[(size_t)i] + panel_split[(size_t)p];
     }
   }
-  // one allocation: nat0, ord0, nat1, ord1
-  size_t off[4], total = 0;
-  for (int g = 0; g < 2; ++g) {
-    off[2 * g] = total;
-    total = align_up(total + nat[g].size() * sizeof(int2), 256);
-    off[2 * g + 1] = total;
-    total = align_up(total + (panel_order ? ord[g].size() * sizeof(int2) : 0), 256);
+}
+
+// Bump allocator over byte offsets, each region 256-byte aligned.
+struct Layout {
+  size_t top = 0;
+  size_t take(size_t bytes, size_t align = 256) {
+    top = align_up(top, align);
+    const size_t at = top;
+    top += bytes;
+    return at;
   }
-  if (dev_malloc(&h->seg_base, total + 256) != cudaSuccess) return ROSKO_ERR_OOM;
-  char* base = static_cast<char*>(h->seg_base);
+};
+
+// The whole pack in two phases with one host round trip:
+//   1. every counting pass (per panel column: Alg. 1's counts; per row: the
+//      row stream; per 128-row tile and column: the gather union), their
+//      scans, and one summary array copied back;
+//   2. the host lays out the handle in one allocation (plus the tile order
+//      and segment lists it derives from the summary, staged in one copy),
+//      then every writing pass runs.
+template <class S, class D>
+rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool quantize_rows,
+                        int32_t dense_min_pm, rosko_packed_s* h, cudaStream_t st) {
+  const int64_t M = h->M, K = h->K, P = h->P;
+  const int64_t n = P * K;
+  const int64_t T = (M + kDenseTileRows - 1) / kDenseTileRows;
+  const bool rows = M > 0 && K < kRowSlotMaxK;
+  const bool gather = rows && h->m_r == 16 && K > 0;
+  const bool dense =
+      std::is_same<D, __nv_bfloat16>::value && dense_min_pm <= 1000 && M > 0 && K > 0;
+  const int64_t nf = gather ? T * K : 0;
+  auto blocks_for = [](int64_t x) { return (x + kScanTile - 1) / kScanTile + 1; };
+
+  // ---- phase 1: counts ------------------------------------------------------
+  Layout s;
+  const size_t o_cnt = s.take((size_t)(n + 1) * sizeof(int2));
+  const size_t o_sums = s.take((size_t)blocks_for(n) * sizeof(int2));
+  const size_t o_touch = s.take((size_t)std::max<int64_t>(K, 1) * sizeof(int));
+  const size_t o_tot = s.take(16);
+  const size_t o_rcnt = s.take(rows ? (size_t)(M + 1) * sizeof(int2) : 0);
+  const size_t o_rsums = s.take(rows ? (size_t)blocks_for(M) * sizeof(int2) : 0);
+  const size_t o_flag = s.take((size_t)(nf + 1) * sizeof(int2));
+  const size_t o_fsums = s.take((size_t)blocks_for(nf) * sizeof(int2));
+  const size_t o_scale = s.take(quantize_rows ? (size_t)M * 4 : 0);
+  const size_t o_sum64 = s.take((size_t)(P + 5) * 8);
+  const size_t o_rp = s.take(rows ? (size_t)(M + 1) * 4 : 0);
+  const size_t summary_bytes = s.top - o_sum64;
+  PoolScratch scr;
+  scr.st = st;
+  if (pool_malloc(&scr.p, s.top + 256, st) != cudaSuccess) return ROSKO_ERR_OOM;
+  char* sb = static_cast<char*>(scr.p);
+  int2* cnt = reinterpret_cast<int2*>(sb + o_cnt);
+  int* touched = reinterpret_cast<int*>(sb + o_touch);
+  int* tot = reinterpret_cast<int*>(sb + o_tot);
+  int2* rcnt = rows ? reinterpret_cast<int2*>(sb + o_rcnt) : nullptr;
+  int2* flag = gather ? reinterpret_cast<int2*>(sb + o_flag) : nullptr;
+
+  // touched flags and totals are adjacent: one memset
+  if (cudaMemsetAsync(touched, 0, o_tot + 16 - o_touch, st) != cudaSuccess ||
+      (n == 0 && cudaMemsetAsync(cnt, 0, sizeof(int2), st) != cudaSuccess))
+    return ROSKO_ERR_CUDA;
+  const float* scale = nullptr;
+  if (quantize_rows) {
+    scale = reinterpret_cast<float*>(sb + o_scale);
+    const int wpb = 8;
+    if (M > 0) {
+      rowscale_kernel<<<(unsigned)((M + wpb - 1) / wpb), wpb * 32, 0, st>>>(
+          reinterpret_cast<const float*>(A), M, K, lda, const_cast<float*>(scale));
+      count_launches(1);
+    }
+  }
+  PackGeom geo;
+  geo.M = M;
+  geo.K = K;
+  geo.lda = lda;
+  geo.P = P;
+  geo.T = T;
+  geo.m_r = h->m_r;
+  geo.gx = (K + kPackThreads - 1) / kPackThreads;
+  const int64_t b_col = n > 0 ? geo.gx * P : 0;
+  const int64_t b_row = rows ? (M + kRowsPerBlock - 1) / kRowsPerBlock : 0;
+  const int64_t b_tile = gather ? geo.gx * T : 0;
+  if (b_col + b_row + b_tile > 0) {
+    pack_count_kernel<S, D><<<(unsigned)(b_col + b_row + b_tile), kPackThreads, 0, st>>>(
+        A, geo, scale, cnt, touched, tot + 2, rcnt, flag, b_col, b_row);
+    count_launches(1);
+  }
+  {
+    ScanSet ss;
+    std::memset(&ss, 0, sizeof(ss));
+    auto add = [&](int2* data, int64_t len, size_t o_s) {
+      if (len <= 0) return;
+      ScanJob& J = ss.job[ss.count];
+      J.data = data;
+      J.n = len;
+      J.sums = reinterpret_cast<int2*>(sb + o_s);
+      J.nb = (len + kScanTile - 1) / kScanTile;
+      ss.first[ss.count + 1] = ss.first[ss.count] + J.nb;
+      ++ss.count;
+    };
+    add(cnt, n, o_sums);
+    if (rows) add(rcnt, M, o_rsums);
+    if (gather) add(flag, nf, o_fsums);
+    if (ss.count > 0) {
+      const unsigned tiles = (unsigned)ss.first[ss.count];
+      scan_reduce_kernel<<<tiles, kScanThreads, 0, st>>>(ss);
+      scan_spine_kernel<<<(unsigned)ss.count, kScanThreads, 0, st>>>(ss);
+      scan_down_kernel<<<tiles, kScanThreads, 0, st>>>(ss);
+      count_launches(3);
+    }
+  }
+  {
+    const int64_t span = std::max<int64_t>(P, M) + 1;
+    pack_summary_kernel<<<(unsigned)((span + 255) / 256), 256, 0, st>>>(
+        cnt, n, P, K, tot + 2, rcnt, M, flag, nf, reinterpret_cast<int64_t*>(sb + o_sum64),
+        rows ? reinterpret_cast<int32_t*>(sb + o_rp) : nullptr);
+    count_launches(1);
+  }
+  std::vector<int64_t> summary((summary_bytes + 7) / 8);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(summary.data(), sb + o_sum64, summary_bytes, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ROSKO_ERR_CUDA;
+
+  // ---- host: sizes, dense tiles, segments, layout ----------------------------
+  h->nnz = summary[0];
+  h->n_cols = summary[1];
+  h->touched_k = summary[2];
+  h->gu_total = gather ? summary[3] : 0;
+  h->panel_nnz.assign(summary.begin() + 4, summary.begin() + 5 + P);
+  const int32_t* rp =
+      rows ? reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(summary.data()) +
+                                              (o_rp - o_sum64))
+           : nullptr;
+  if (dense) plan_dense_tiles(h, dense_min_pm);
+  std::vector<int2> nat[2], ord[2];
+  if (rows) plan_segments(h, rp, dense ? &h->panel_order_host : nullptr, nat, ord);
+
+  const size_t rsz = rec_size(h->dt);
+  const int64_t nnz = h->nnz, n_cols = h->n_cols;
+  Layout L;
+  // staged from the host in one copy
+  const size_t o_to = L.take(dense ? (size_t)T * 4 : 0);
+  const size_t o_po = L.take(dense ? (size_t)P * 4 : 0);
+  size_t o_seg[4];
   for (int g = 0; g < 2; ++g) {
-    rosko_packed_s::SegList& L = h->segs[g];
-    L.nat = reinterpret_cast<int2*>(base + off[2 * g]);
-    L.ord = panel_order ? reinterpret_cast<int2*>(base + off[2 * g + 1]) : nullptr;
-    if (cudaMemcpyAsync(L.nat, nat[g].data(), nat[g].size() * sizeof(int2),
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        (panel_order && cudaMemcpyAsync(L.ord, ord[g].data(), ord[g].size() * sizeof(int2),
-                                        cudaMemcpyHostToDevice, st) != cudaSuccess))
+    o_seg[2 * g] = L.take(nat[g].size() * sizeof(int2));
+    o_seg[2 * g + 1] = L.take(ord[g].size() * sizeof(int2));
+  }
+  const size_t staged = L.top;
+  // written on the device
+  const size_t o_pc = L.take((size_t)(P + 1) * 4);
+  const size_t o_pn = L.take((size_t)(P + 1) * 8);
+  const size_t o_rs = L.take((size_t)std::max<int64_t>(M, 1) * 4);
+  const size_t o_ft = L.take(256);
+  const size_t o_cr = L.take((size_t)(n_cols + 2) * 8);
+  const size_t o_nz = L.take((size_t)(nnz + 1) * rsz);
+  const size_t o_rowptr = L.take(rows ? (size_t)(M + 1) * 4 : 0);
+  const size_t o_rnz = L.take(rows ? (size_t)(nnz + M) * rsz : 0);
+  const size_t o_gs = L.take(gather ? (size_t)(T + 1) * 4 : 0);
+  const size_t o_gk = L.take(gather ? (size_t)std::max<int64_t>(h->gu_total, 1) * 4 : 0);
+  const size_t o_gnz = L.take(gather ? (size_t)(nnz + M) * rsz : 0);
+  const size_t o_da =
+      L.take(dense ? (size_t)h->n_copy * kDenseTileRows * (size_t)h->Kpad * 2 : 0, 1024);
+  if (pool_malloc(&h->base, L.top + 256, st) != cudaSuccess) return ROSKO_ERR_OOM;
+  char* b = static_cast<char*>(h->base);
+  h->panel_col = reinterpret_cast<int32_t*>(b + o_pc);
+  h->panel_nnz_dev = reinterpret_cast<int64_t*>(b + o_pn);
+  h->row_scale = reinterpret_cast<float*>(b + o_rs);
+  h->feat_dev = reinterpret_cast<float*>(b + o_ft);
+  h->colrec = reinterpret_cast<int2*>(b + o_cr);
+  h->nz = b + o_nz;
+  if (rows) {
+    h->rowptr = reinterpret_cast<int32_t*>(b + o_rowptr);
+    h->rnz = b + o_rnz;
+    for (int g = 0; g < 2; ++g) {
+      h->segs[g].nat = reinterpret_cast<int2*>(b + o_seg[2 * g]);
+      h->segs[g].ord = dense ? reinterpret_cast<int2*>(b + o_seg[2 * g + 1]) : nullptr;
+    }
+  }
+  if (gather) {
+    h->gu_start = reinterpret_cast<int32_t*>(b + o_gs);
+    h->gu_k = reinterpret_cast<int32_t*>(b + o_gk);
+    h->gnz = b + o_gnz;
+  }
+  if (dense) {
+    h->tile_order_dev = reinterpret_cast<int32_t*>(b + o_to);
+    h->panel_order_dev = reinterpret_cast<int32_t*>(b + o_po);
+    h->dense_A = b + o_da;
+  }
+  if (staged > 0) {
+    std::vector<char> stage(staged, 0);
+    if (dense) {
+      std::memcpy(stage.data() + o_to, h->tile_order.data(), (size_t)T * 4);
+      std::memcpy(stage.data() + o_po, h->panel_order_host.data(), (size_t)P * 4);
+    }
+    for (int g = 0; g < 2; ++g) {
+      if (!nat[g].empty())
+        std::memcpy(stage.data() + o_seg[2 * g], nat[g].data(), nat[g].size() * sizeof(int2));
+      if (!ord[g].empty())
+        std::memcpy(stage.data() + o_seg[2 * g + 1], ord[g].data(), ord[g].size() * sizeof(int2));
+    }
+    // a pageable source is staged before the call returns
+    if (cudaMemcpyAsync(b, stage.data(), staged, cudaMemcpyHostToDevice, st) != cudaSuccess)
       return ROSKO_ERR_CUDA;
   }
-  if (cudaStreamSynchronize(st) != cudaSuccess) return ROSKO_ERR_CUDA;
+
+  // ---- phase 2: writes ------------------------------------------------------
+  if (quantize_rows) {
+    if (M > 0 && cudaMemcpyAsync(h->row_scale, scale, (size_t)M * 4, cudaMemcpyDeviceToDevice,
+                                 st) != cudaSuccess)
+      return ROSKO_ERR_CUDA;
+  } else if (h->dt == ROSKO_I8 && M > 0) {
+    if (scale_in) {
+      if (cudaMemcpyAsync(h->row_scale, scale_in, (size_t)M * 4, cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess)
+        return ROSKO_ERR_CUDA;
+    } else {
+      fill_kernel<<<(unsigned)std::min<int64_t>((M + 255) / 256, 1024), 256, 0, st>>>(
+          h->row_scale, M, 1.0f);
+      count_launches(1);
+    }
+  }
+  WriteArgs w;
+  std::memset(&w, 0, sizeof(w));
+  w.cnt = cnt;
+  w.colrec = h->colrec;
+  w.nz = h->nz;
+  w.panel_col = h->panel_col;
+  w.panel_nnz = h->panel_nnz_dev;
+  w.rcnt = rcnt;
+  w.rowptr = h->rowptr;
+  w.rnz = h->rnz;
+  w.flag = flag;
+  w.gu_start = h->gu_start;
+  w.gu_k = h->gu_k;
+  w.gnz = h->gnz;
+  w.nnz = nnz;
+  w.n_cols = n_cols;
+  w.gu_total = h->gu_total;
+  w.zero_panels = n == 0 ? 1 : 0;
+  w.b_scatter = b_col;
+  w.b_row = b_row;
+  w.b_union = b_tile;
+  if (dense && h->n_copy > 0) {
+    w.tile_order = h->tile_order_dev;
+    w.dense_A = reinterpret_cast<__nv_bfloat16*>(h->dense_A);
+    w.dense_rows = h->n_copy * kDenseTileRows;
+    w.Kpad = h->Kpad;
+    w.gxd = (h->Kpad + kPackThreads - 1) / kPackThreads;
+    w.ry = std::min<int64_t>(w.dense_rows, 2048);
+    w.b_dense = w.gxd * w.ry;
+  }
+  pack_write_kernel<S, D>
+      <<<(unsigned)(w.b_scatter + w.b_row + w.b_union + w.b_dense + 1), kPackThreads, 0, st>>>(
+          A, geo, scale, w);
+  count_launches(1);
+  // the scratch is released on return: wait for the writes that read it
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return ROSKO_ERR_CUDA;
   return ROSKO_OK;
 }
 
@@ -858,35 +991,22 @@ rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, in
   h->P = (M + m_r - 1) / m_r;
   h->dt = p_dt;
   rosko_status s = ROSKO_ERR_UNSUPPORTED;
+  const int32_t dm = dense_min_pm;
   if (a_dt == ROSKO_F32 && p_dt == ROSKO_F32)
-    s = pack_typed<float, float>((const float*)A, M, K, lda, nullptr, false, h, stream);
+    s = pack_typed<float, float>((const float*)A, lda, nullptr, false, dm, h, stream);
   else if (a_dt == ROSKO_F32 && p_dt == ROSKO_BF16)
-    s = pack_typed<float, __nv_bfloat16>((const float*)A, M, K, lda, nullptr, false, h, stream);
+    s = pack_typed<float, __nv_bfloat16>((const float*)A, lda, nullptr, false, dm, h, stream);
   else if (a_dt == ROSKO_F32 && p_dt == ROSKO_F64)
-    s = pack_typed<float, double>((const float*)A, M, K, lda, nullptr, false, h, stream);
+    s = pack_typed<float, double>((const float*)A, lda, nullptr, false, dm, h, stream);
   else if (a_dt == ROSKO_F32 && p_dt == ROSKO_I8)
-    s = pack_typed<float, int8_t>((const float*)A, M, K, lda, nullptr, true, h, stream);
+    s = pack_typed<float, int8_t>((const float*)A, lda, nullptr, true, dm, h, stream);
   else if (a_dt == ROSKO_BF16 && p_dt == ROSKO_BF16)
-    s = pack_typed<__nv_bfloat16, __nv_bfloat16>((const __nv_bfloat16*)A, M, K, lda, nullptr,
-                                                 false, h, stream);
+    s = pack_typed<__nv_bfloat16, __nv_bfloat16>((const __nv_bfloat16*)A, lda, nullptr, false, dm,
+                                                 h, stream);
   else if (a_dt == ROSKO_I8 && p_dt == ROSKO_I8)
-    s = pack_typed<int8_t, int8_t>((const int8_t*)A, M, K, lda, row_scale_in, false, h, stream);
-  if (s == ROSKO_OK && p_dt == ROSKO_BF16 && dense_min_pm <= 1000) {
-    if (a_dt == ROSKO_F32)
-      s = build_dense_tiles<float>((const float*)A, lda, dense_min_pm, h, stream);
-    else
-      s = build_dense_tiles<__nv_bfloat16>((const __nv_bfloat16*)A, lda, dense_min_pm, h,
-                                           stream);
-  }
-  if (s == ROSKO_OK)
-    s = build_segments(h, h->panel_order_dev ? &h->panel_order_host : nullptr, stream);
+    s = pack_typed<int8_t, int8_t>((const int8_t*)A, lda, row_scale_in, false, dm, h, stream);
   if (s != ROSKO_OK) {
-    if (h->seg_base) cudaFree(h->seg_base);
-    if (h->meta_base) cudaFree(h->meta_base);
-    if (h->data_base) cudaFree(h->data_base);
-    if (h->dense_base) cudaFree(h->dense_base);
-    if (h->row_base) cudaFree(h->row_base);
-    if (h->gather_base) cudaFree(h->gather_base);
+    pool_free(h->base, stream);
     delete h;
     return s;
   }

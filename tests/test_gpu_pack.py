@@ -118,15 +118,20 @@ def test_pack_empty_shapes():
 
 
 def test_alloc_failure_is_reported(monkeypatch):
-    # host-side fault injection: each of the packer's three device
-    # allocations fails in turn and is reported as ROSKO_ERR_OOM
+    # host-side fault injection: each of the packer's two device allocations
+    # (pass-1 scratch, then the handle) fails in turn and is reported as
+    # ROSKO_ERR_OOM; there is no third
     rosko = built()
     A = torch.randn(40, 40, device="cuda")
-    for n in ("1", "2", "3"):
+    for n in ("1", "2"):
         monkeypatch.setenv("ROSKO_FAIL_ALLOC", n)
         with pytest.raises(rosko.RoskoError) as ei:
             rosko.rosko_pack(A, 0)
         assert ei.value.status == 3
+    for dt in (rosko.F32, rosko.BF16):
+        monkeypatch.setenv("ROSKO_FAIL_ALLOC", "3" if dt == rosko.F32 else "4")
+        h = rosko.rosko_pack(A, dt)
+        assert h.info()["nnz"] == int((A != 0).sum())
     monkeypatch.delenv("ROSKO_FAIL_ALLOC")
     h = rosko.rosko_pack(A, 0)
     assert h.info()["nnz"] == int((A != 0).sum())
@@ -150,3 +155,27 @@ def test_pack_transposed_is_the_pack_of_the_transpose(dt, M, K):
     assert h1.info() == h2.info()
     B = gen.normal((M, 70), gen.rng_for(92, M))
     check(dt, *run(rosko, np.ascontiguousarray(A.T), B, dt, m_r=0))
+
+
+@pytest.mark.parametrize("a_dt,p_dt", PAIRS)
+def test_pack_launch_count(a_dt, p_dt):
+    # the independent passes of each phase share one launch: counting (panel
+    # columns, rows, tile columns), the three launches of the fused scans,
+    # the size summary, then writing (column records, row and gather streams,
+    # union lists, dense copies, terminating entries); INT8 adds its row
+    # scales (quantisation from FP32, or the all-ones default)
+    rosko = built()
+    A = _matrix(300, 500, 0.9, seed=5)
+    if a_dt == "bf16":
+        At = torch.from_numpy(A).to(torch.bfloat16).cuda()
+    elif a_dt == "i8":
+        At = torch.from_numpy(np.clip(np.rint(A * 40), -127, 127).astype(np.int8)).cuda()
+    else:
+        At = torch.from_numpy(A).cuda()
+    torch.cuda.synchronize()
+    l0 = rosko.rosko_kernel_launches()
+    h = rosko.rosko_pack(At, CODES[p_dt])
+    assert rosko.rosko_kernel_launches() - l0 == 6 + (p_dt == "i8")
+    nnz = int((At != 0).sum())
+    # quantisation from FP32 also drops the values whose code rounds to 0
+    assert h.info()["nnz"] == nnz if a_dt == p_dt or p_dt != "i8" else h.info()["nnz"] <= nnz

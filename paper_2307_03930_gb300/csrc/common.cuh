@@ -162,12 +162,6 @@ int* device_status_word();
 // Device allocation with the test-only failure hook (ROSKO_FAIL_ALLOC=n makes
 // the n-th allocation of the process fail).
 cudaError_t dev_malloc(void** p, size_t bytes);
-// Stream-ordered allocation from the library's own memory pool on the current
-// device (freed blocks stay mapped, up to 256 MiB per device, so repeated packs
-// skip mapping fresh memory); pool_free releases in the order of `st`.  Both
-// honour the allocation-failure test hook of dev_malloc.
-cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
-void pool_free(void* p, cudaStream_t st);
 // cuTensorMapEncodeTiled obtained through the runtime (no libcuda link).
 CUresult encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank, void* gaddr,
                       const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box,

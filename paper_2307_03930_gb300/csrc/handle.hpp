@@ -121,6 +121,13 @@ inline size_t rec_size(rosko_dtype d) {
 }
 inline bool handle_ok(const rosko_packed_s* h) { return h && h->magic == kHandleMagic; }
 
+// api.cu: stream-ordered allocation from the library's own memory pool on
+// the current device (freed blocks stay mapped, up to 256 MiB per device, so
+// repeated packs skip mapping fresh memory); pool_free releases in the order
+// of `st`.  Both honour the allocation-failure test hook of dev_malloc.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t st);
+void pool_free(void* p, cudaStream_t st);
+
 // pack.cu
 constexpr int kDenseTileRows = 128;
 rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,

@@ -3,15 +3,18 @@
 // Alg. 1 walks a tile column by column and, within a column, row by row,
 // appending each nonzero to A_p / loc_m and, for a non-empty column, its
 // index to col_ind and its count to nnz.  On the GPU the per-(panel, column)
-// counts are independent, so the walk becomes three passes:
-//   1. count   one thread per (panel, column): nonzeros of that panel column
-//   2. scan    exclusive prefix sums of (count, count != 0) in panel-major,
-//              column-ascending order = Alg. 1's append order
-//   3. scatter one thread per (panel, column): writes its column record and
-//              its values/rows (rows ascending) at the scanned offsets
-// Threads of a warp own consecutive columns, so every read of A is a
-// coalesced row segment.  The packer is bound by reading A (twice: count and
-// scatter) and writing the packed stream.
+// counts are independent, so the walk becomes count / scan / scatter:
+//   count   one thread per (panel, column): nonzeros of that panel column
+//   scan    exclusive prefix sums of (count, count != 0) in panel-major,
+//           column-ascending order = Alg. 1's append order
+//   scatter one thread per (panel, column): writes its column record and
+//           its values/rows (rows ascending) at the scanned offsets
+// The execution layouts of the SpMM (row stream, touched-row gather, dense
+// BF16 tile copies) are built the same way, and the independent passes share
+// launches: phase 1 is one counting launch and one three-array scan, phase 2
+// one writing launch, with one host round trip between them (pack_typed).
+// Threads of a warp own consecutive columns (or, for row passes, one warp owns
+// a row), so every read of A is a coalesced row segment.
 #include <algorithm>
 #include <cstring>
 #include <new>

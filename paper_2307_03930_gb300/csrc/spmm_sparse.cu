@@ -20,6 +20,7 @@
 //     contiguous 512-byte run (conflict free);
 //   * C is written once at the end (or added with atomics when K is split
 //     across CTAs).
+#include <type_traits>
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -542,6 +543,8 @@ __global__ void __launch_bounds__(256, 3)
   // B type)
   constexpr int U = 4;
   static_assert(J * CE == V, "V must be a multiple of the chunk width");
+  constexpr bool kDp4a = std::is_same<TB, int8_t>::value && std::is_same<TACC, int32_t>::value &&
+                         U == 4 && CE == 8 && J == 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int q = 0;
   while (q + 1 < T.count && (int64_t)blockIdx.x >= T.p[q + 1].blocks0) ++q;
@@ -632,8 +635,34 @@ __global__ void __launch_bounds__(256, 3)
           for (int jj = 0; jj < J; ++jj) raw[u][jj] = RawT{};
         }
       }
+      if constexpr (kDp4a) {
+        // INT8: the four records' B rows (eight INT8 columns per lane each)
+        // are transposed by byte permutes into one 4-byte word per column
+        // (the four rows' bytes) and multiplied with the four A codes by one
+        // 4-way byte dot product per column - exact, like the IMAD chain
+        uint32_t ap = 0;
 #pragma unroll
-      for (int u = 0; u < U; ++u) fma_raw(t + u < cnt ? RowRec<TA>::a(w[u]) : TACC(0), raw[u]);
+        for (int u = 0; u < U; ++u)
+          ap |= (t + u < cnt ? ((uint32_t)w[u] >> 16) & 0xFFu : 0u) << (8 * u);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t q0 = h ? raw[0][0].y : raw[0][0].x;
+          const uint32_t q1 = h ? raw[1][0].y : raw[1][0].x;
+          const uint32_t q2 = h ? raw[2][0].y : raw[2][0].x;
+          const uint32_t q3 = h ? raw[3][0].y : raw[3][0].x;
+          const uint32_t lo01 = __byte_perm(q0, q1, 0x5140);   // q0.b0 q1.b0 q0.b1 q1.b1
+          const uint32_t lo23 = __byte_perm(q2, q3, 0x5140);
+          const uint32_t hi01 = __byte_perm(q0, q1, 0x7362);   // q0.b2 q1.b2 q0.b3 q1.b3
+          const uint32_t hi23 = __byte_perm(q2, q3, 0x7362);
+          acc[4 * h + 0] = __dp4a((int)__byte_perm(lo01, lo23, 0x5410), (int)ap, acc[4 * h + 0]);
+          acc[4 * h + 1] = __dp4a((int)__byte_perm(lo01, lo23, 0x7632), (int)ap, acc[4 * h + 1]);
+          acc[4 * h + 2] = __dp4a((int)__byte_perm(hi01, hi23, 0x5410), (int)ap, acc[4 * h + 2]);
+          acc[4 * h + 3] = __dp4a((int)__byte_perm(hi01, hi23, 0x7632), (int)ap, acc[4 * h + 3]);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) fma_raw(t + u < cnt ? RowRec<TA>::a(w[u]) : TACC(0), raw[u]);
+      }
     }
   }
   // C written once (dequantisation needs the scales of this problem)

@@ -65,6 +65,10 @@ def parse():
     return a
 
 
+# nominal HBM3e bandwidth of a GB300 (the measured copy peak is the roofline)
+NOMINAL_HBM_GBS = 7900.0
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -376,10 +380,23 @@ def main():
                 "rowdirect_kernel" if pl["dense_tiles"] == 0 else "dense_panel+rowdirect")
         if pl["dense_tiles"] == 0 and pl["order"] != 4:
             kern = f"sparse_spmm_kernel(order {pl['order']})"
-        per.append({"sparsity": s, "nnz": nnz[i], "ms": per_kernel_ms[i], "kernel": kern,
-                    "plan": pl, "gflops": 2.0 * nnz[i] * N / t / 1e9, "alg_bytes": bytes_alg,
-                    "hbm_gbs": bytes_alg / t / 1e9,
-                    "hbm_frac": bytes_alg / t / 1e9 / pk["hbm_gbs"]})
+        gflops = 2.0 * nnz[i] * N / t / 1e9
+        # arithmetic peak of the kernel: the BF16 tensor peak for the
+        # tensor-core path, the FP32 FFMA peak for the CUDA-core traversals
+        arith = pk["bf16_tflops"] if kern.startswith("dense") else fp32_peak_tflops
+        row = {"sparsity": s, "nnz": nnz[i], "ms": per_kernel_ms[i], "kernel": kern,
+               "plan": pl, "gflops": gflops, "alg_bytes": bytes_alg,
+               "hbm_gbs": bytes_alg / t / 1e9,
+               "hbm_frac": bytes_alg / t / 1e9 / pk["hbm_gbs"],
+               "hbm_frac_nominal": bytes_alg / t / 1e9 / NOMINAL_HBM_GBS,
+               "alu_frac": gflops / 1e3 / arith, "alu_peak_tflops": arith}
+        if pl["dense_tiles"] > 0:
+            # the work the tensor cores do: every row of the dense tiles
+            # times K times N, zeros included
+            dense_rows = min(M, pl["dense_tiles"] * 128)
+            row["tensor_work_tflops"] = 2.0 * dense_rows * K * N / t / 1e12
+            row["tensor_work_frac"] = row["tensor_work_tflops"] / pk["bf16_tflops"]
+        per.append(row)
     # the dominant kernel: largest share of the per-kernel time of a step
     kinds = {}
     for r in per:
@@ -412,6 +429,12 @@ def main():
     roof["launches_per_step"] = dk["launches_per_step"]
     roof["per_launch_ms"] = dk["ms"] / dk["launches_per_step"]
     roof["alg_bytes_per_launch"] = dk["alg_bytes"] / dk["launches_per_step"]
+    if dom_name.startswith("dense"):
+        # beside the roofline of the algorithmic work: the tensor cores'
+        # own work (dense tiles, zeros included) against the BF16 peak
+        tw = [r["tensor_work_tflops"] * r["ms"] for r in per
+              if r["kernel"] == dom_name and "tensor_work_tflops" in r]
+        roof["tensor_work_frac"] = sum(tw) / dk["ms"] / pk["bf16_tflops"]
     roof["peak_source"] = (f"{pk['source']} (MEASURED_PEAKS.json)" if roof["bound"] in ("hbm", "tensor")
                            else f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x "
                                 f"{pk['sm_max_mhz']:.0f} MHz")

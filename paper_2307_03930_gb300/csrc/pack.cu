@@ -292,23 +292,52 @@ struct PackGeom {
 
 // Counting pass, Alg. 1's per-column nnz: cnt[p*K + k] = (nonzeros of column
 // k in panel p, 1 if non-empty); a column's first nonzero seen anywhere
-// counts it as touched.
+// counts it as touched.  The same visit of the panel yields the other two
+// counts: the nonzeros of each row (a ballot per row across the warp, summed
+// over the block in shared memory, one atomic add per row and block into
+// rcnt, which starts at 0; the block of columns 0..255 adds the row's
+// sentinel) and, for the gather stream, flag[t*K + k].x = 1 when column k of
+// 128-row tile t is non-empty (flag starts at 0).
 template <class S, class D>
 __device__ void col_count(const S* __restrict__ A, const PackGeom& g,
                           const float* __restrict__ scale, int64_t b, int2* __restrict__ cnt,
-                          int* __restrict__ touched, int* __restrict__ touched_total) {
-  const int64_t k = (b % g.gx) * kPackThreads + threadIdx.x;
+                          int* __restrict__ touched, int* __restrict__ touched_total,
+                          int2* __restrict__ rcnt, int2* __restrict__ flag) {
+  __shared__ int row_sum[32];   // m_r <= 32
+  const int64_t bx = b % g.gx;
+  const int64_t k = bx * kPackThreads + threadIdx.x;
   const int64_t p = b / g.gx;
-  if (k >= g.K) return;
+  const bool in = k < g.K;
+  const int lane = threadIdx.x & 31;
   const int64_t m0 = p * g.m_r, m1 = min(g.M, m0 + g.m_r);
+  if (rcnt) {
+    if (threadIdx.x < 32) row_sum[threadIdx.x] = 0;
+    __syncthreads();
+  }
   int c = 0;
+  // bounds are uniform across the block: every lane takes every ballot
 #pragma unroll 8
   for (int64_t m = m0; m < m1; ++m) {
     D v;
-    c += Conv<S, D>::get(A[m * g.lda + k], scale ? scale[m] : 1.0f, v) ? 1 : 0;
+    const bool nz = in && Conv<S, D>::get(A[m * g.lda + k], scale ? scale[m] : 1.0f, v);
+    c += nz ? 1 : 0;
+    if (rcnt) {
+      const unsigned mask = __ballot_sync(0xffffffffu, nz);
+      if (lane == 0 && mask) atomicAdd(&row_sum[m - m0], __popc(mask));
+    }
   }
+  if (rcnt) {
+    __syncthreads();
+    const int64_t r = m0 + threadIdx.x;
+    if (threadIdx.x < 32 && r < m1) {
+      const int add = row_sum[threadIdx.x] + (bx == 0 ? 1 : 0);
+      if (add) atomicAdd(&rcnt[r].x, add);
+    }
+  }
+  if (!in) return;
   cnt[p * g.K + k] = make_int2(c, c != 0);
   if (c && atomicExch(&touched[k], 1) == 0) atomicAdd(touched_total, 1);
+  if (c && flag) flag[(m0 / kDenseTileRows) * g.K + k] = make_int2(1, 0);
 }
 
 // Counting pass of the row-slot stream: rcnt[row] = (nonzeros of the row + 1
@@ -330,49 +359,21 @@ __device__ void row_count(const S* __restrict__ A, const PackGeom& g,
   if (lane == 0) rcnt[row] = make_int2(c + 1, 0);
 }
 
-// Counting pass of the gather stream: flag[t*K + k] = (1 if any row of
-// 128-row tile t has a nonzero in column k, 0).
-template <class S, class D>
-__device__ void tile_flag(const S* __restrict__ A, const PackGeom& g,
-                          const float* __restrict__ scale, int64_t b, int2* __restrict__ flag) {
-  const int64_t k = (b % g.gx) * kPackThreads + threadIdx.x;
-  const int64_t t = b / g.gx;
-  if (k >= g.K) return;
-  const int64_t m0 = t * kDenseTileRows, m1 = min(g.M, m0 + kDenseTileRows);
-  int any = 0;
-  // sixteen rows per step, loads issued together (no early exit, which would
-  // serialise them)
-  for (int64_t m = m0; m < m1; m += 16) {
-#pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      if (m + u < m1) {
-        D v;
-        any |= Conv<S, D>::get(A[(m + u) * g.lda + k], scale ? scale[m + u] : 1.0f, v) ? 1 : 0;
-      }
-    }
-  }
-  flag[t * g.K + k] = make_int2(any, 0);
-}
-
-// Phase 1 in one launch: blocks [0, b_col) count panel columns, the next
-// b_row blocks count rows, the rest flag tile columns.
+// Phase 1 in one launch: blocks [0, b_col) count panel columns (and rows and
+// tile columns, see col_count); with K = 0 there are no column blocks and
+// the remaining blocks give each row its sentinel count instead.
 template <class S, class D>
 __global__ void __launch_bounds__(kPackThreads)
     pack_count_kernel(const S* __restrict__ A, PackGeom g, const float* __restrict__ scale,
                       int2* __restrict__ cnt, int* __restrict__ touched,
                       int* __restrict__ touched_total, int2* __restrict__ rcnt,
-                      int2* __restrict__ flag, int64_t b_col, int64_t b_row) {
-  int64_t b = blockIdx.x;
+                      int2* __restrict__ flag, int64_t b_col) {
+  const int64_t b = blockIdx.x;
   if (b < b_col) {
-    col_count<S, D>(A, g, scale, b, cnt, touched, touched_total);
+    col_count<S, D>(A, g, scale, b, cnt, touched, touched_total, rcnt, flag);
     return;
   }
-  b -= b_col;
-  if (b < b_row) {
-    row_count<S, D>(A, g, scale, b, rcnt);
-    return;
-  }
-  tile_flag<S, D>(A, g, scale, b - b_row, flag);
+  row_count<S, D>(A, g, scale, b - b_col, rcnt);
 }
 
 // Pointers and block ranges of the writing phase.  Scanned offsets:
@@ -734,8 +735,9 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
   int2* rcnt = rows ? reinterpret_cast<int2*>(sb + o_rcnt) : nullptr;
   int2* flag = gather ? reinterpret_cast<int2*>(sb + o_flag) : nullptr;
 
-  // touched flags and totals are adjacent: one memset
-  if (cudaMemsetAsync(touched, 0, o_tot + 16 - o_touch, st) != cudaSuccess ||
+  // touched flags, totals, row counts (and their tile sums) and tile flags
+  // are adjacent: one memset
+  if (cudaMemsetAsync(touched, 0, o_fsums - o_touch, st) != cudaSuccess ||
       (n == 0 && cudaMemsetAsync(cnt, 0, sizeof(int2), st) != cudaSuccess))
     return ROSKO_ERR_CUDA;
   const float* scale = nullptr;
@@ -757,13 +759,17 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
   geo.m_r = h->m_r;
   geo.gx = (K + kPackThreads - 1) / kPackThreads;
   const int64_t b_col = n > 0 ? geo.gx * P : 0;
-  const int64_t b_row = rows ? (M + kRowsPerBlock - 1) / kRowsPerBlock : 0;
-  const int64_t b_tile = gather ? geo.gx * T : 0;
-  if (b_col + b_row + b_tile > 0) {
-    pack_count_kernel<S, D><<<(unsigned)(b_col + b_row + b_tile), kPackThreads, 0, st>>>(
-        A, geo, scale, cnt, touched, tot + 2, rcnt, flag, b_col, b_row);
+  // rows are counted by the column blocks; without columns (K = 0) every row
+  // still gets its sentinel from a row block
+  const int64_t b_row_count = (rows && n == 0) ? (M + kRowsPerBlock - 1) / kRowsPerBlock : 0;
+  if (b_col + b_row_count > 0) {
+    pack_count_kernel<S, D><<<(unsigned)(b_col + b_row_count), kPackThreads, 0, st>>>(
+        A, geo, scale, cnt, touched, tot + 2, rcnt, flag, b_col);
     count_launches(1);
   }
+  // the writing phase's ranges
+  const int64_t b_row = rows ? (M + kRowsPerBlock - 1) / kRowsPerBlock : 0;
+  const int64_t b_tile = gather ? geo.gx * T : 0;
   {
     ScanSet ss;
     std::memset(&ss, 0, sizeof(ss));

@@ -136,8 +136,6 @@ rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, in
 rosko_status transpose_impl(const void* A, rosko_dtype dt, int64_t M, int64_t K, int64_t lda,
                             void* out, cudaStream_t st);
 rosko_status unpack_impl(rosko_packed_s* h, void* A_out, int64_t lda, cudaStream_t stream);
-rosko_status count_nonzeros(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
-                            cudaStream_t st, int64_t* out);
 constexpr int64_t kRowSlotMaxK = 65280;  // sentinel k = 0xFFFF stays past every slab end
 
 // spmm_sparse.cu

@@ -105,21 +105,6 @@ __device__ __forceinline__ int get_row(const void* nz, int64_t e, double) {
   return reinterpret_cast<const RecF64*>(nz)[e].r;
 }
 
-// Nonzero count of A (before packing, to choose the default panel height).
-template <class S>
-__global__ void nnz_count_kernel(const S* __restrict__ A, int64_t M, int64_t K, int64_t lda,
-                                 unsigned long long* __restrict__ out) {
-  unsigned long long c = 0;
-  const int64_t total = M * K;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = i / K, k = i - m * K;
-    c += (to_f32(A[m * lda + k]) != 0.0f) ? 1 : 0;
-  }
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
-}
-
 // Per-row symmetric INT8 scale s_i = max_k |a_ik| / 127 (1 for an all-zero row).
 __global__ void rowscale_kernel(const float* __restrict__ A, int64_t M, int64_t K, int64_t lda,
                                 float* __restrict__ scale) {
@@ -559,13 +544,6 @@ __global__ void unpack_kernel(const int32_t* __restrict__ panel_col,
       out[(p * m_r + get_row(nz, e, D())) * lda + k] = get_val(nz, e, D());
   }
 }
-
-struct Scratch {
-  void* p = nullptr;
-  ~Scratch() {
-    if (p) cudaFree(p);
-  }
-};
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -1021,31 +999,6 @@ rosko_status pack_impl(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, in
   }
   h->magic = kHandleMagic;
   *out = h;
-  return ROSKO_OK;
-}
-
-rosko_status count_nonzeros(const void* A, rosko_dtype a_dt, int64_t M, int64_t K, int64_t lda,
-                            cudaStream_t st, int64_t* out) {
-  *out = 0;
-  if (M == 0 || K == 0) return ROSKO_OK;
-  Scratch scr;
-  if (dev_malloc(&scr.p, 256) != cudaSuccess) return ROSKO_ERR_OOM;
-  auto* d = static_cast<unsigned long long*>(scr.p);
-  if (cudaMemsetAsync(d, 0, 8, st) != cudaSuccess) return ROSKO_ERR_CUDA;
-  const int64_t total = M * K;
-  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4 * 1024);
-  if (a_dt == ROSKO_F32)
-    nnz_count_kernel<float><<<blocks, 256, 0, st>>>((const float*)A, M, K, lda, d);
-  else if (a_dt == ROSKO_BF16)
-    nnz_count_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)A, M, K, lda, d);
-  else
-    return ROSKO_ERR_UNSUPPORTED;
-  count_launches(1);
-  unsigned long long v = 0;
-  if (cudaMemcpyAsync(&v, d, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return ROSKO_ERR_CUDA;
-  *out = (int64_t)v;
   return ROSKO_OK;
 }
 

@@ -40,7 +40,7 @@ extern "C" {
 typedef enum {
   ROSKO_OK = 0,
   ROSKO_ERR_INVALID_ARG = 1,  /* bad size, pointer, dtype, alignment or tile   */
-  ROSKO_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement   */
+  ROSKO_ERR_UNSUPPORTED = 2,  /* valid request the library does not implement */
   ROSKO_ERR_OOM = 3,          /* a device allocation failed                    */
   ROSKO_ERR_CUDA = 4,         /* a CUDA runtime/driver call failed             */
   ROSKO_ERR_TIMEOUT = 5,      /* a bounded device wait ran out                 */

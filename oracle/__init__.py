@@ -17,10 +17,9 @@ quant     BF16 round-to-nearest-even and symmetric INT8 quantisers.
 features  Schedule-selector input features of a sparse A and N.
 mlp       The selector's 3x64 ReLU MLP: forward, softmax cross-entropy,
           backward and one Adam step, in FP64.
-tiles     Eq. 1-3 (on-chip memory and bandwidth model) as plain formulas.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against hand-derived examples, brute force, closed forms or invariants; none
 is "parity unpinned".
 """
-from . import pack, spmm, quant, features, mlp, tiles  # noqa: F401
+from . import pack, spmm, quant, features, mlp  # noqa: F401

@@ -1,4 +1,4 @@
-"""Pins for the oracle's precision handling, selector features and Eq. 1-3."""
+"""Pins for the oracle's precision handling and selector features."""
 import math
 
 import numpy as np
@@ -7,7 +7,6 @@ import torch
 
 from oracle.quant import bf16_round, bf16_bits, quantize_rows_int8, quantize_cols_int8
 from oracle.features import features, N_FEATURES
-from oracle import tiles
 
 
 def test_bf16_hand_cases():
@@ -83,17 +82,3 @@ def test_features_hand_case():
     assert abs(f[13] - np.sqrt(np.mean((pn - 6.5) ** 2)) / 6.5) < 1e-15
     assert f[14] == math.log2(1 + 13 / 12)
     assert f[15] == 0.0
-
-
-def test_eq1_eq3_closed_forms():
-    L3 = 20 * 2 ** 20 // 4
-    for d in [0.01, 0.1, 0.5]:
-        m = tiles.eq1_max_mc(d, 10, L3)
-        assert tiles.eq1_lhs(d, 10, m, m) <= L3 < tiles.eq1_lhs(d, 10, m + 1, m + 1)
-    # Eq. 2 at d = 1: (3 + 1) / m_c * peak
-    assert tiles.eq2_bw(1.0, 100, 8.0) == pytest.approx(0.32)
-    # Eq. 2 grows as density falls (Sec. 4.2)
-    assert tiles.eq2_bw(0.01, 100, 1.0) > tiles.eq2_bw(0.1, 100, 1.0)
-    assert tiles.outer_product_intensity(8, 8) == 4.0        # mn/(m+n), Sec. 2.1
-    assert tiles.outer_product_intensity(10, 5, d=0.5) == 2.5  # d m n/(d m + n)
-    assert tiles.eq3_lhs(0.5, 4, 10, 8) == 3 * 0.5 * 4 * 10 + 80 + 32

@@ -112,5 +112,38 @@ def test_normalized_error_zero_denominator():
     assert normalized_error([[1.5]], [[1.0]], [[2.0]]) == 0.25
 
 
-def test_flops():
-    assert flops(104858, 1024) == 2 * 104858 * 1024
+def _count_macs(A, N):
+    """Multiply-accumulates of the row-skipping product, counted one by one:
+    every (i, k, j) with A[i, k] != 0 is one product a_ik * b_kj added into
+    c_ij (Sec. 3); rows with a zero a_ik are skipped and cost nothing."""
+    count = 0
+    M, K = len(A), len(A[0])
+    for i in range(M):
+        for k in range(K):
+            if A[i][k] != 0:
+                for _ in range(N):
+                    count += 1
+    return count
+
+
+def test_flops_against_counted_macs():
+    # Sec. 5 counts one FLOP per multiply-accumulate (nnz * N); the metric
+    # here counts the multiply and the add (2 * nnz * N).  The hand example
+    # of tests/golden has 4 nonzeros and N = 2: 8 products, 16 flops.
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "hand_example.json")) as f:
+        ex = json.load(f)
+    A = ex["A"]
+    N = len(ex["B"][0])
+    nnz = sum(1 for r in A for x in r if x != 0)
+    assert _count_macs(A, N) == 8
+    assert flops(nnz, N) == 2 * _count_macs(A, N) == 16
+    # random shapes, including an all-zero row and an all-zero matrix
+    rng = np.random.default_rng(11)
+    for M, K, N in [(5, 7, 3), (1, 9, 4), (6, 2, 1), (3, 3, 5)]:
+        Ar = np.where(rng.random((M, K)) < 0.4, rng.standard_normal((M, K)), 0.0)
+        Ar[0] = 0.0
+        nz = int(np.count_nonzero(Ar))
+        assert flops(nz, N) == 2 * _count_macs(Ar.tolist(), N)
+    assert flops(0, 17) == 2 * _count_macs([[0.0, 0.0]], 17) == 0

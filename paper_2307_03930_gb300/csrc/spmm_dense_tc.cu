@@ -384,6 +384,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           // conflicts) so that each store instruction writes 32 consecutive
           // columns of one row
           float* tr = reinterpret_cast<float*>(my_stage);
+          // the staging tiles may still be read by this warp's TMA stores of
+          // an earlier problem of the batch (one with aligned C rows): wait
+          // until those reads are done before reusing the space
+          if (lane == 0) bulk_wait_read<0>();
           __syncwarp();
 #pragma unroll
           for (int j = 0; j < 32; ++j) tr[lane * 32 + ((j + lane) & 31)] = __uint_as_float(r[j]);

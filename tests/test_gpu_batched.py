@@ -111,3 +111,43 @@ def test_batched_fp32_row_direct_is_one_launch(accumulate):
             D = D + np.abs(C0s[j])
         assert normalized_error(C.cpu().numpy(), ref, D) <= 1e-5, j
     assert launches == 1
+
+
+def test_c4_full_size_batch_under_graph_replay():
+    """The 64 uneven layers the benchmark times (seed 3: M, K log-uniform in
+    [64, 4096], N in [196, 12544], sparsity uniform in [0.70, 0.99], BF16,
+    uniform masks, post-ReLU B), run by one rosko_spmm_batched call captured
+    in a CUDA graph and replayed; every problem's C is compared with the
+    oracle on 16 sampled rows (all columns)."""
+    rosko = built()
+    seed = 3
+    shapes = gen.c4_shapes(seed, 64)
+    hs, Bs, Cs, probs = [], [], [], []
+    for j, (M_, K_, N_, s_) in enumerate(shapes):
+        A = gen.sparse_weight(M_, K_, s_, gen.rng_for(seed, 1, j), "uniform")
+        B = gen.relu_normal((K_, N_), gen.rng_for(seed, 2, j))
+        hs.append(rosko.rosko_pack(torch.from_numpy(A).cuda(), rosko.BF16))
+        Bs.append(_ldpad(torch.from_numpy(B).to(torch.bfloat16), 2))
+        Cs.append(torch.full((M_, N_), float("nan"), device="cuda"))
+        probs.append((A, B))
+    # first call uncaptured (it resolves and caches what capture must not do)
+    rosko.rosko_spmm_batched(hs, Bs, Cs)
+    torch.cuda.synchronize()
+    for C in Cs:
+        C.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rosko.rosko_spmm_batched(hs, Bs, Cs)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert rosko.rosko_device_status(clear=True) == 0
+    worst = 0.0
+    for j, ((A, B), C) in enumerate(zip(probs, Cs)):
+        M_ = A.shape[0]
+        rows = np.unique(np.random.default_rng(1000 + j).integers(0, M_, 16))
+        ref, D = spmm(bf16_round(A[rows]), bf16_round(B))
+        err = normalized_error(C[torch.from_numpy(rows).cuda()].cpu().numpy(), ref, D)
+        worst = max(worst, err)
+        assert err <= 1e-5, (j, shapes[j], err)
+    assert worst <= 1e-5

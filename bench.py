@@ -185,64 +185,113 @@ KERNEL_SRC = {
 
 
 # ----------------------------------------------------------------------------
-def cpu_baseline(budget_s: float = 12.0):
-    """The oracle as it stands, on a bounded row sample of every sparsity."""
+# The oracle on the host cores: one worker process per core (started with
+# `spawn`, since the parent has used the GPU), each holding the sweep's inputs
+# and running the oracle as it stands on the row samples it is handed.
+_W = {}
+
+
+def _oracle_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    _W["inputs"] = make_inputs(0)
+
+
+def _oracle_rows(task):
+    """Oracle rows of one sparsity; returns their flops (2 nnz N)."""
     from oracle.spmm import spmm
-    As, Bs = make_inputs(0)
-    flops = 0.0
-    t0 = time.perf_counter()
-    rows_done = {s: 0 for s in SPARSITIES}
-    rng = np.random.default_rng(0)
-    order = rng.permutation(M)
-    per = budget_s / len(SPARSITIES)
-    for i, s in enumerate(SPARSITIES):
-        t1 = time.perf_counter()
-        j = 0
-        while time.perf_counter() - t1 < per and j < M:
-            r = order[j:j + 4]
-            spmm(As[i], Bs[i], rows=r)
-            flops += 2.0 * np.count_nonzero(As[i][r]) * N
-            j += 4
-        rows_done[s] = j
-    dt = time.perf_counter() - t0
-    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+    i, rows = task
+    As, Bs = _W["inputs"]
+    spmm(As[i], Bs[i], rows=np.asarray(rows))
+    return 2.0 * float(np.count_nonzero(As[i][np.asarray(rows)])) * N
+
+
+def _oracle_ready(_):
+    return "inputs" in _W
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover - not Linux
+        return os.cpu_count() or 1
+
+
+def oracle_pool():
+    import multiprocessing as mp
+    cores = host_cores()
+    pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init)
+    # every worker has built its inputs before anything is timed
+    while not all(pool.map(_oracle_ready, range(4 * cores), chunksize=1)):
+        pass
+    return pool, cores
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The oracle as it stands, on a bounded row sample of every sparsity,
+    spread over all host cores (rows of a sparsity, 4 at a time, dealt to the
+    workers; the sample ends once `budget_s` seconds of wall time have
+    passed)."""
+    pool, cores = oracle_pool()
+    try:
+        rng = np.random.default_rng(0)
+        order = rng.permutation(M)
+        tasks = [(i, order[j:j + 4].tolist()) for j in range(0, M, 4)
+                 for i in range(len(SPARSITIES))]
+        flops = 0.0
+        rows_done = {s: 0 for s in SPARSITIES}
+        t0 = time.perf_counter()
+        t_end = t0
+        for (i, rows), f in zip(tasks, pool.imap(_oracle_rows, tasks, chunksize=1)):
+            flops += f
+            rows_done[SPARSITIES[i]] += len(rows)
+            t_end = time.perf_counter()
+            if t_end - t0 > budget_s:
+                break
+        dt = t_end - t0
+    finally:
+        pool.terminate()
+        pool.join()
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
             "sample": ("rows " + ", ".join(f"{int(round(s * 1000)) / 10}%:{rows_done[s]}/{M}"
                                            for s in SPARSITIES)
-                       + f" of the sweep, FP64 numpy oracle, {dt:.1f} s")}
+                       + f" of the sweep, FP64 numpy oracle, {cores} worker processes, "
+                         f"{dt:.1f} s")}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle on all host cores, each step a bounded
+    sample of the sweep (per sparsity, 2 rows per worker)."""
     if rank != 0:
         return
-    steps = args.steps
-    # each step: a bounded sample (~2 s) of the sweep through the oracle
+    steps = max(1, args.steps)
+    warm = args.warmup
+    pool, cores = oracle_pool()
     t_total = 0.0
     flops = 0.0
-    from oracle.spmm import spmm
-    As, Bs = make_inputs(0)
-    # every step is ~0.2 s of oracle work, so the requested counts are kept
-    steps = max(1, steps)
-    warm = args.warmup
-    for it in range(warm + steps):
-        t0 = time.perf_counter()
-        f = 0.0
-        for i, s in enumerate(SPARSITIES):
-            r = np.arange((it * 3) % M, (it * 3) % M + 2) % M
-            spmm(As[i], Bs[i], rows=r)
-            f += 2.0 * np.count_nonzero(As[i][r]) * N
-        dt = time.perf_counter() - t0
-        if it >= warm:
-            t_total += dt
-            flops += f
+    try:
+        for it in range(warm + steps):
+            base = (it * 2 * cores) % M
+            tasks = [(i, [(base + 2 * w) % M, (base + 2 * w + 1) % M])
+                     for i in range(len(SPARSITIES)) for w in range(cores)]
+            t0 = time.perf_counter()
+            f = sum(pool.map(_oracle_rows, tasks, chunksize=1))
+            dt = time.perf_counter() - t0
+            if it >= warm:
+                t_total += dt
+                flops += f
+    finally:
+        pool.terminate()
+        pool.join()
     v = flops / t_total / 1e9
+    sample = f"{2 * cores} rows of each of the 6 sparsities per step ({cores} workers x 2 rows)"
     line = {"metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": world, "steps": steps,
             "warmup": warm, "ms_per_step": t_total / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "2 rows per sparsity per step",
-                       "parallelism": "host, one core"},
-            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": "2 rows of each of the 6 sparsities per step"},
+            "config": {"workload": WORKLOAD, "sample": sample,
+                       "parallelism": f"host, {cores} cores (one oracle process per core)"},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -445,6 +494,7 @@ def main():
     if not args.no_extras:
         extras = comparison_legs(rosko, torch, dev, sets, infos, stream)
         extras["batched_uneven_layers"] = batched_leg(rosko, torch, dev)
+        extras["training_step"] = training_leg(rosko, torch, dev, sets)
         extras["pack"] = pack_leg(rosko, torch, dev, sets)
         extras["other_configs"] = other_configs_leg(rosko, torch, dev)
 
@@ -649,12 +699,29 @@ def comparison_legs(rosko, torch, dev, sets, infos, stream):
     B32 = [torch.from_numpy(b).to(dev) for b in sets[0]["B_np"]]
     B16 = sets[0]["B16"]
     Cs = sets[0]["C"]
+    pk = peaks()
+    out["footprint"] = []
     for i, s in enumerate(SPARSITIES):
         A32 = torch.from_numpy(sets[0]["A_np"][i]).to(dev)
         fl = 2.0 * infos[i]["nnz"] * N
         h32 = rosko.rosko_pack(A32, rosko.F32)
+        i32 = h32.info()
         ms = cycled_time(lambda j: rosko.rosko_spmm(h32, B32[j], Cs[j]), torch)
-        out["fp32_plain"].append({"sparsity": s, "ms": ms, "gflops": fl / ms / 1e6})
+        # the FP32 form's own roofline: FP32 packed A + touched FP32 B rows +
+        # C, against the measured HBM peak
+        b32 = i32["bytes"] + i32["touched_k"] * N * 4 + M * N * 4
+        out["fp32_plain"].append({"sparsity": s, "ms": ms, "gflops": fl / ms / 1e6,
+                                  "alg_bytes": b32, "hbm_gbs": b32 / ms / 1e6,
+                                  "hbm_frac": b32 / ms / 1e6 / pk["hbm_gbs"]})
+        # device footprint of the packed handles against dense and CSR storage
+        nz = infos[i]["nnz"]
+        out["footprint"].append({
+            "sparsity": s, "bf16_handle_device_bytes": infos[i]["device_bytes"],
+            "bf16_column_format_bytes": infos[i]["bytes"],
+            "fp32_handle_device_bytes": i32["device_bytes"],
+            "fp32_column_format_bytes": i32["bytes"],
+            "dense_bf16_bytes": M * K * 2, "dense_fp32_bytes": M * K * 4,
+            "csr_fp32_bytes": nz * 8 + (M + 1) * 4, "csr_bf16_bytes": nz * 6 + (M + 1) * 4})
         Acsr = A32.to_sparse_csr()
         cnt = [0]
 
@@ -672,23 +739,35 @@ def comparison_legs(rosko, torch, dev, sets, infos, stream):
         del h32, Acsr
     del B32
     for k in list(out):
+        if not isinstance(out[k], list):
+            continue
         rows = [r for r in out[k] if "ms" in r]
         if rows:
             tot = sum(r["ms"] for r in rows)
             fl = sum(2.0 * infos[i]["nnz"] * N for i in range(len(rows)))
             out[k + "_sweep_gflops"] = fl / tot / 1e6
+    r32 = out["fp32_plain"]
+    tot = sum(r["ms"] for r in r32)
+    byt = sum(r["alg_bytes"] for r in r32)
+    out["fp32_roofline"] = {"bound": "hbm", "kernel": "rowdirect_kernel (FP32)",
+                            "achieved": byt / tot / 1e6, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                            "frac": byt / tot / 1e6 / pk["hbm_gbs"],
+                            "note": "whole FP32 sweep: algorithmic bytes / summed kernel time"}
     return out
 
 
 def batched_leg(rosko, torch, dev, seed=3, count=64):
     """Uneven layers (64 SpMMs: M, K log-uniform in [64, 4096], N in
     [196, 12544], sparsity uniform in [0.70, 0.99], BF16): one
-    rosko_spmm_batched call (one persistent tensor-core launch per tile shape
-    plus one row-direct launch) captured in a CUDA graph, against 64 separate
-    rosko_spmm calls captured in a graph and issued from the host."""
+    rosko_spmm_batched call captured in a CUDA graph, with the analytic rule's
+    tiles and with per-shape tiles from rosko_autotune, against 64 separate
+    rosko_spmm calls captured in a graph and issued from the host; beside
+    them the per-problem roofline sum, sum_i max(bytes_i / HBM peak,
+    2 nnz_i N_i / BF16 peak)."""
     from paper_2307_03930_gb300 import inputs as gen
+    pk = peaks()
     shapes = gen.c4_shapes(seed, count)
-    hs, Bs, Cs, flops = [], [], [], 0.0
+    hs, Bs, Cs, flops, roof_s = [], [], [], 0.0, 0.0
     for j, (M_, K_, N_, s_) in enumerate(shapes):
         A = gen.sparse_weight(M_, K_, s_, gen.rng_for(seed, 1, j), "uniform")
         h = rosko.rosko_pack(torch.from_numpy(A).to(dev), rosko.BF16)
@@ -699,20 +778,31 @@ def batched_leg(rosko, torch, dev, seed=3, count=64):
         hs.append(h)
         Bs.append(Bbuf[:, :N_])
         Cs.append(torch.empty((M_, N_), device=dev))
-        flops += 2.0 * h.info()["nnz"] * N_
+        inf = h.info()
+        fl = 2.0 * inf["nnz"] * N_
+        flops += fl
+        byt = inf["bytes"] + inf["touched_k"] * N_ * 2 + M_ * N_ * 4
+        roof_s += max(byt / (pk["hbm_gbs"] * 1e9), fl / (pk["bf16_tflops"] * 1e12))
     work_mb = sum(b.numel() * 2 + c.numel() * 4 for b, c in zip(Bs, Cs)) / 1e6
+    tuned = [rosko.rosko_autotune(h, b, c)[0] for h, b, c in zip(hs, Bs, Cs)]
 
     def batched():
         rosko.rosko_spmm_batched(hs, Bs, Cs)
+
+    def batched_tuned():
+        rosko.rosko_spmm_batched(hs, Bs, Cs, tiles=tuned)
 
     def separate():
         for h, b, c in zip(hs, Bs, Cs):
             rosko.rosko_spmm(h, b, c)
 
-    out = {"problems": count, "gflop": flops / 1e9, "working_set_mb": work_mb}
-    for name, fn in (("batched_graph", batched), ("separate_graph", separate)):
+    out = {"problems": count, "gflop": flops / 1e9, "working_set_mb": work_mb,
+           "roofline_sum_ms": roof_s * 1e3}
+    for name, fn in (("batched_graph", batched), ("batched_autotuned_graph", batched_tuned),
+                     ("separate_graph", separate)):
         out[name + "_ms"] = graph_time(fn, torch, reps=5)
         out[name + "_gflops"] = flops / (out[name + "_ms"] * 1e-3) / 1e9
+        out[name + "_roofline_frac"] = roof_s * 1e3 / out[name + "_ms"]
     for _ in range(2):
         separate()
     torch.cuda.synchronize()
@@ -728,6 +818,39 @@ def batched_leg(rosko, torch, dev, seed=3, count=64):
     batched()
     out["batched_kernel_launches"] = rosko.rosko_kernel_launches() - l0
     torch.cuda.synchronize()
+    return out
+
+
+def training_leg(rosko, torch, dev, sets):
+    """The SpMMs of a pruned layer's training step (Sec. 5.4): the forward
+    O = W X with the packed W, the input gradient dX = W^T dO with W^T packed
+    by rosko_pack_transposed, and that re-pack itself (paid once per pruning
+    epoch, when the mask changes), on the 512 x 4608 layer with 3136 columns,
+    BF16, at 90% and 99%."""
+    out = []
+    dO = [torch.randn((M, N), device=dev).to(torch.bfloat16) for _ in range(6)]
+    dX = [torch.empty((K, N), device=dev) for _ in range(6)]
+    for i, s in enumerate(SPARSITIES):
+        if s not in (0.9, 0.99):
+            continue
+        W = torch.from_numpy(sets[0]["A_np"][i]).to(dev)
+        hT = rosko.rosko_pack_transposed(W, rosko.BF16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            h2 = rosko.rosko_pack_transposed(W, rosko.BF16)
+            torch.cuda.synchronize()
+            del h2
+        repack_ms = (time.perf_counter() - t0) / 5 * 1e3
+        nnz = hT.info()["nnz"]
+        ms_t = cycled_time(lambda j: rosko.rosko_spmm(hT, dO[j], dX[j]), torch)
+        plan = rosko.rosko_spmm_plan(hT, dO[0], dX[0])
+        out.append({"sparsity": s, "transposed_spmm_ms": ms_t,
+                    "transposed_spmm_gflops": 2.0 * nnz * N / ms_t / 1e6,
+                    "transposed_dense_tiles": plan["dense_tiles"],
+                    "transposed_sparse_panels": plan["sparse_panels"],
+                    "repack_transposed_ms": repack_ms})
+        del hT, W
     return out
 
 

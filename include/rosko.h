@@ -253,6 +253,16 @@ rosko_status rosko_packed_info(rosko_packed_t A, int64_t* nnz, int64_t* bytes,
                                int32_t* packed_dtype, int64_t* n_cols);
 
 /*
+ * rosko_packed_shape - M and K of the packed matrix and the handle's whole
+ * device footprint in bytes: every layout the pack builds (column records,
+ * row stream and work segments, touched-row gather, dense BF16 tile copies,
+ * scales, bookkeeping) in its single device allocation; rosko_packed_info's
+ * `bytes` counts only the Rosko column format.  Any pointer may be NULL.
+ * Host data only.
+ */
+rosko_status rosko_packed_shape(rosko_packed_t A, int64_t* M, int64_t* K, int64_t* device_bytes);
+
+/*
  * rosko_packed_export - copy the canonical Alg. 1 arrays to host buffers,
  * concatenated over panels in panel order (synchronous):
  *   A_p_host   nnz values (packed dtype)       loc_m_host  nnz uint8 rows
@@ -263,6 +273,35 @@ rosko_status rosko_packed_info(rosko_packed_t A, int64_t* nnz, int64_t* bytes,
 rosko_status rosko_packed_export(rosko_packed_t A, void* A_p_host, uint8_t* loc_m_host,
                                  int32_t* col_ind_host, int32_t* nnz_host,
                                  int64_t* panel_cols_host);
+
+/*
+ * rosko_pack_save - write a packed handle to a host byte image, so that a
+ * pre-packed weight (Sec. 4.1: weights of an inference layer are packed once
+ * and stored) can be restored by rosko_pack_load without re-packing.
+ * buf_host  destination (host memory), or NULL to query the size only.
+ * capacity  bytes available at buf_host (ignored for a size query).
+ * bytes     receives the image size (always set on ROSKO_OK).
+ * Image: little-endian; a versioned header (magic "ROSKOKP1", format 1), the
+ * handle's host bookkeeping, its device allocation byte for byte, and an
+ * FNV-1a 64-bit checksum of all of it.  It records the packed dtype, m_r and
+ * the dense-copy threshold the pack used.  Synchronous (one device-to-host
+ * copy).  Errors: ROSKO_ERR_BAD_HANDLE, ROSKO_ERR_INVALID_ARG (capacity too
+ * small), ROSKO_ERR_CUDA.
+ */
+rosko_status rosko_pack_save(rosko_packed_t A, void* buf_host, int64_t capacity, int64_t* bytes);
+
+/*
+ * rosko_pack_load - a new handle on the current device from an image written
+ * by rosko_pack_save (any device, any process).  The image is checked before
+ * any device work: a wrong magic, a bad checksum, a truncated image or
+ * inconsistent sizes give ROSKO_ERR_INVALID_ARG, another format version
+ * ROSKO_ERR_UNSUPPORTED; *out is NULL on error.  The restored handle is
+ * identical to the saved one (same bytes on the device), so every SpMM gives
+ * bit-identical results.  Device memory comes from the library's pool.
+ * Synchronises `stream`.
+ */
+rosko_status rosko_pack_load(const void* buf_host, int64_t bytes, rosko_stream_t stream,
+                             rosko_packed_t* out);
 
 /*
  * rosko_schedule_analytic - the closed-form tile rule (host only, no GPU
@@ -325,7 +364,8 @@ rosko_status rosko_time_tile(rosko_packed_t A, const void* B_dev, rosko_dtype b_
  * fractions of rows in four row-density bins (100 r < K, 20 r < K <= 100 r,
  * 5 r < K <= 20 r, K <= 5 r for row nnz r), mean fraction of non-empty
  * columns per panel, panel-nnz coefficient of variation, log2(1 + nnz per
- * packed column), fraction of empty panels.  Synchronises.
+ * packed column), fraction of empty panels.  Synchronises.  The handle's
+ * device must be current (else ROSKO_ERR_INVALID_ARG, nothing launched).
  */
 rosko_status rosko_features(rosko_packed_t A, int64_t N, double* features16, rosko_stream_t stream);
 
@@ -341,9 +381,14 @@ rosko_status rosko_features(rosko_packed_t A, int64_t N, double* features16, ros
  * Allocates no device memory and does not synchronise.  Limits and races:
  *   - A->M must be <= 1048576 (the static array's rows), else
  *     ROSKO_ERR_INVALID_ARG before anything is enqueued;
- *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current): make it once before
- *     any stream capture;
+ *   - the handle's device must be current (else ROSKO_ERR_INVALID_ARG);
+ *   - every call outside a stream capture looks up the array's device
+ *     address on the current device (cudaGetSymbolAddress); a call inside a
+ *     capture uses the address found by that device's last uncaptured call,
+ *     so make one call on each device before capturing (and again after a
+ *     cudaDeviceReset, which invalidates the address);
+ *   - the features are FP32 arithmetic on exact integer counts: they agree
+ *     with rosko_features to FP32 rounding (a relative 1e-5 or better);
  *   - every call shares the one array per device and clears it first, so
  *     calls that can overlap on the GPU (different streams, or several host
  *     threads) race and may return wrong features: serialise them.
@@ -392,6 +437,25 @@ rosko_status rosko_selector_set(const float* params_host, int64_t n_params, cons
  * stream.  Synchronises the device.
  */
 rosko_status rosko_device_status(int32_t* bits, int clear);
+
+/*
+ * rosko_set_wait_limit - the time after which every bounded wait of this
+ * library's kernels on the current device gives up (sets status bit 1, see
+ * rosko_device_status, and lets its kernel return).  ns > 0 sets it, ns = 0
+ * restores the default of 2 s; ns < 0 is ROSKO_ERR_INVALID_ARG.  Synchronous;
+ * launches already queued read the new value when their waits start.
+ */
+rosko_status rosko_set_wait_limit(int64_t ns);
+
+/*
+ * rosko_probe_bounded_wait - diagnostic launch of the failure-detection
+ * path: one CTA waits on an mbarrier that nothing completes, with the same
+ * bounded wait every pipelined kernel of the library uses; after the current
+ * device's wait limit it sets status bit 1 and returns, leaving the context
+ * usable.  Ordered on `stream`, does not synchronise.  With the default limit
+ * the launch takes about 2 s: set a short limit first.
+ */
+rosko_status rosko_probe_bounded_wait(rosko_stream_t stream);
 
 /*
  * rosko_kernel_launches - number of CUDA kernels this library has launched

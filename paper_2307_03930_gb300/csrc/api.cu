@@ -95,6 +95,21 @@ void pool_free(void* p, cudaStream_t st) {
 namespace {
 std::atomic<int64_t> g_launches{0};
 }
+
+// Failure-detection probe: an mbarrier expecting two arrivals gets one, so
+// its phase never completes and the bounded wait runs out.
+__global__ void probe_wait_kernel(int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  if (threadIdx.x == 0) mbar_arrive(&bar);
+  __syncwarp();
+  if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, status);
+  __syncwarp();
+}
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int* device_status_word() {
@@ -172,13 +187,13 @@ void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, i
 // Density (per mille) from which a 128-row tile runs on the tensor cores.
 // Sec. 4.2 balances work against bandwidth; here the balance is between two
 // engines: a dense tile costs 2*128*K*N tensor-core flops, its sparse form
-// 2*nnz*N CUDA-core flops, so the break-even density is the ratio of the
-// two engines' effective rates.  Measured on GB300 for a 512 x 4608 x 3136
-// layer: ~460 TFLOP/s of dense work for the stream-K tcgen05 kernel against
-// ~2-3 TFLOP/s effective for the row-skipping kernel at 99% sparsity, so the
-// break-even sits near 5 per mille (the autotuner and the selector refine it
-// per shape).
-constexpr int kDenseSplitPm = 5;
+// moves nnz*N B values from L2 into the row-direct kernel, so the break-even
+// density is the ratio of the two engines' effective rates.  Measured on
+// GB300 for a 512 x 4608 x 3136 layer: ~0.8 PFLOP/s of dense work for the
+// stream-K tcgen05 kernel against ~12 TB/s of B bytes for the row-direct
+// kernel (BF16: 2 bytes per multiply-add), i.e. d = 12e12 / 0.8e15 = 1.5%
+// (the autotuner and the selector refine it per shape).
+constexpr int kDenseSplitPm = 15;
 constexpr int kDenseCopyPm = 1;
 
 // ---------------------------------------------------------------------------
@@ -231,27 +246,15 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
   t->split_k = (int32_t)split;
   t->dense_split_pm = (dt == ROSKO_BF16) ? kDenseSplitPm : 1001;
   if (dt == ROSKO_BF16 && order == 4) {
-    // Small layers: the tensor-core launch has a fixed cost (~6 us: set-up,
-    // the first cold loads, the epilogue) that row-direct (~3 us) does not.
-    // Model both on the uniform-density assumption (every tile dense at
-    // d >= 5 per mille) and keep the layer sparse when row-direct is
-    // predicted faster.  Dense: work at ~0.8 PFLOP/s.  Row-direct: nnz * N
-    // BF16 values from L2 at ~5 TB/s, plus its latency chain: a warp walks
-    // one row piece (of the length picked below) four records per ~0.8 us
-    // round trip, and ~24 warps per SM are resident.
+    // Small or very sparse layers: the tensor-core launch has a fixed cost
+    // (~6 us: set-up, the first cold loads, the epilogue).  Model both paths
+    // on the uniform-density assumption (every tile on one side of the
+    // threshold) and keep the layer sparse when row-direct is predicted
+    // faster.  Dense: work at ~0.8 PFLOP/s.  Row-direct (fitted to the
+    // 512 x 4608 x 3136 sweep from 90% to 99.8%): ~6 us plus the nnz * N
+    // BF16 values it moves from L2 at ~12 TB/s.
     const double t_dense = 6.0 + 2.0 * (double)M * (double)K * (double)N / 0.8e15 * 1e6;
-    const double row = M ? (double)nnz / (double)M : 0.0;
-    // the piece length a launch would pick (coarse if it still gives four
-    // waves of resident warps, else kSegRecords)
-    const double strips = std::ceil((double)N / 256.0);
-    double seg = (double)seg_records_for(nnz, M);
-    if ((double)M * std::max(1.0, std::ceil(row / seg)) * strips < 4.0 * 24.0 * sms)
-      seg = kSegRecords;
-    const double pieces = std::max(1.0, std::ceil(row / seg));
-    const double warps = (double)M * pieces * strips;
-    const double waves = std::ceil(warps / (24.0 * sms));
-    const double chain = 0.8 * std::ceil(std::min(row, seg) / 4.0) * waves;
-    const double t_direct = 3.0 + (double)nnz * (double)N * 2.0 / 5e12 * 1e6 + chain;
+    const double t_direct = 6.0 + (double)nnz * (double)N * 2.0 / 12e12 * 1e6;
     if (t_direct < t_dense) t->dense_split_pm = 1001;
   }
   int TN = 256, ds = 1;
@@ -361,6 +364,25 @@ void rosko_free(rosko_packed_t A) {
     if (other) cudaSetDevice(cur);
   }
   delete A;
+}
+
+rosko_status rosko_pack_save(rosko_packed_t A, void* buf_host, int64_t capacity, int64_t* bytes) {
+  if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
+  if (!bytes || (buf_host && capacity < 0)) return ROSKO_ERR_INVALID_ARG;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return ROSKO_ERR_CUDA;
+  if (buf_host && cur != A->device && cudaSetDevice(A->device) != cudaSuccess) return ROSKO_ERR_CUDA;
+  const rosko_status s = packed_serialize(A, buf_host, capacity, bytes);
+  if (buf_host && cur != A->device) cudaSetDevice(cur);
+  return s;
+}
+
+rosko_status rosko_pack_load(const void* buf_host, int64_t bytes, rosko_stream_t stream,
+                             rosko_packed_t* out) {
+  if (!out) return ROSKO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!buf_host || bytes <= 0) return ROSKO_ERR_INVALID_ARG;
+  return packed_deserialize(buf_host, bytes, static_cast<cudaStream_t>(stream), out);
 }
 
 rosko_status rosko_schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int32_t m_r,
@@ -867,6 +889,14 @@ rosko_status rosko_packed_info(rosko_packed_t A, int64_t* nnz, int64_t* bytes, i
   return ROSKO_OK;
 }
 
+rosko_status rosko_packed_shape(rosko_packed_t A, int64_t* M, int64_t* K, int64_t* device_bytes) {
+  if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
+  if (M) *M = A->M;
+  if (K) *K = A->K;
+  if (device_bytes) *device_bytes = (int64_t)A->base_bytes;
+  return ROSKO_OK;
+}
+
 rosko_status rosko_packed_export(rosko_packed_t A, void* A_p_host, uint8_t* loc_m_host,
                                  int32_t* col_ind_host, int32_t* nnz_host,
                                  int64_t* panel_cols_host) {
@@ -990,6 +1020,10 @@ rosko_status rosko_features(rosko_packed_t A, int64_t N, double* features16,
                             rosko_stream_t stream) {
   if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
   if (!features16 || N < 1) return ROSKO_ERR_INVALID_ARG;
+  // the feature kernels read the handle's arrays: only on its own device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ROSKO_ERR_CUDA;
+  if (dev != A->device) return ROSKO_ERR_INVALID_ARG;
   return features_impl(A, N, features16, static_cast<cudaStream_t>(stream));
 }
 
@@ -998,6 +1032,9 @@ rosko_status rosko_features_static(rosko_packed_t A, int64_t N, float* features1
   if (!handle_ok(A)) return ROSKO_ERR_BAD_HANDLE;
   if (!features16_dev || N < 1 || reinterpret_cast<uintptr_t>(features16_dev) % 4 != 0)
     return ROSKO_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ROSKO_ERR_CUDA;
+  if (dev != A->device) return ROSKO_ERR_INVALID_ARG;
   return features_static_impl(A, N, features16_dev, static_cast<cudaStream_t>(stream));
 }
 
@@ -1046,6 +1083,25 @@ rosko_status rosko_selector_set(const float* params_host, int64_t n_params, cons
 }
 
 int64_t rosko_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rosko_status rosko_set_wait_limit(int64_t ns) {
+  if (ns < 0) return ROSKO_ERR_INVALID_ARG;
+  int* w = device_status_word();
+  if (!w) return ROSKO_ERR_CUDA;
+  const unsigned long long v = (unsigned long long)ns;
+  return cudaMemcpy(reinterpret_cast<char*>(w) + kWaitLimitOffset, &v, sizeof(v),
+                    cudaMemcpyHostToDevice) == cudaSuccess
+             ? ROSKO_OK
+             : ROSKO_ERR_CUDA;
+}
+
+rosko_status rosko_probe_bounded_wait(rosko_stream_t stream) {
+  int* w = device_status_word();
+  if (!w) return ROSKO_ERR_CUDA;
+  probe_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(w);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+}
 
 rosko_status rosko_device_status(int32_t* bits, int clear) {
   if (!bits) return ROSKO_ERR_INVALID_ARG;

@@ -23,13 +23,14 @@ struct SparseCand {
 // Sparse-path configurations (m_r comes from the pack, n_r from the order
 // unless V is given).
 const SparseCand kSparse[] = {
-    {2, 4, 64, 1, 0}, {2, 4, 64, 4, 0}, {2, 8, 32, 2, 0}, {2, 8, 128, 1, 0},
+    {2, 4, 64, 1, 0}, {2, 4, 64, 4, 0}, {2, 8, 32, 2, 0}, {4, 1, 8, 1, 16},
     {3, 8, 64, 1, 0}, {3, 8, 128, 2, 0}, {3, 8, 128, 4, 0}, {3, 8, 256, 8, 0},
     {1, 4, 64, 1, 0}, {1, 8, 32, 4, 0}, {4, 1, 8, 1, 4}, {4, 1, 8, 1, 8},
 };
 constexpr int kNumSparse = sizeof(kSparse) / sizeof(kSparse[0]);
-// Dense-split thresholds in per mille (1001 = never).
-const int kDensePm[] = {1001, 1, 5, 20, 60};
+// Dense-split thresholds in per mille (1001 = never); 15 is the analytic
+// rule's break-even density.
+const int kDensePm[] = {1001, 1, 5, 15, 60};
 constexpr int kNumDense = sizeof(kDensePm) / sizeof(kDensePm[0]);
 
 }  // namespace

@@ -15,8 +15,12 @@ namespace rosko {
 constexpr int kStatusTimeout = 1;   // a bounded wait gave up
 constexpr int kStatusCorrupt = 2;   // packed stream inconsistent with the handle
 
-// Bounded waits give up after this many nanoseconds of %globaltimer.
+// Bounded waits give up after this many nanoseconds of %globaltimer, unless
+// the per-device wait limit (rosko_set_wait_limit: the 64-bit word that
+// follows the status word, 0 = this default) says otherwise.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+// Byte offset of the wait limit in the per-device status allocation.
+constexpr int kWaitLimitOffset = 8;
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -65,14 +69,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete.  Gives up after
-// kWaitLimitNs, records kStatusTimeout in *status and returns false.
+// The wait limit of the device whose status word is `status`.
+__device__ __forceinline__ unsigned long long wait_limit_ns(const int* status) {
+  if (!status) return kWaitLimitNs;
+  const unsigned long long v = *reinterpret_cast<const volatile unsigned long long*>(
+      reinterpret_cast<const char*>(status) + kWaitLimitOffset);
+  return v ? v : kWaitLimitNs;
+}
+
+// Wait for the phase with the given parity to complete.  Gives up after the
+// device's wait limit, records kStatusTimeout in *status and returns false.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
+  const unsigned long long limit = wait_limit_ns(status);
   for (uint32_t spin = 1;; ++spin) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((spin & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+    if ((spin & 255u) == 0 && global_ns() - t0 > limit) {
       if (status) atomicOr(status, kStatusTimeout);
       return false;
     }

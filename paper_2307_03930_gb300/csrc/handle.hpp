@@ -53,6 +53,7 @@ struct rosko_packed_s {
   rosko_dtype dt = ROSKO_F32;
   int64_t nnz = 0, n_cols = 0, touched_k = 0;
   void* base = nullptr;  // one device allocation holding every array below
+  size_t base_bytes = 0;  // its size
   int32_t* panel_col = nullptr;
   int2* colrec = nullptr;
   void* nz = nullptr;
@@ -71,13 +72,15 @@ struct rosko_packed_s {
   // 0 cuts every row into pieces of at most kSegRecords nonzeros (many
   // warps for few or long rows), list 1 only rows longer than
   // seg_records_for (twice the mean; few atomics for even matrices).  Per
-  // list: {row, piece} per segment in row order (nat) and in panel_order
+  // list: one int4 {row, first record, end record, cut} per segment (the
+  // record range of the piece in the row stream, sentinel excluded; cut = 1
+  // when the row has several pieces) in row order (nat) and in panel_order
   // order (ord, BF16 packs with dense copies); prefix[i] / split[i] count the
   // segments / the panels with a cut row among the first i panels of
   // panel_order (or of the natural order without one).
   struct SegList {
-    int2* nat = nullptr;
-    int2* ord = nullptr;
+    int4* nat = nullptr;
+    int4* ord = nullptr;
     std::vector<int64_t> prefix;
     std::vector<int32_t> split;
     int32_t records = kSegRecords;
@@ -179,7 +182,7 @@ struct DirectJob {
 // is of another kind.  *cut: some listed row is cut into several pieces
 // (their sums are added into C, which must then be zeroed unless the call
 // accumulates).
-const int2* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
+const int4* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
                             int which, int64_t* n_segs, bool* cut);
 // The list a launch over these panels with width N and V columns per lane
 // uses (0 fine, 1 coarse); decided the same way for zero-fill and launch.
@@ -244,6 +247,11 @@ rosko_status autotune_impl(rosko_packed_s* h, const void* B, rosko_dtype b_dt, i
                            int64_t ldb, const float* col_scale, void* C, rosko_dtype c_dt,
                            int64_t ldc, int reps, rosko_tile* best, float* times,
                            int32_t* n_out, cudaStream_t st);
+
+// serialize.cu
+rosko_status packed_serialize(const rosko_packed_s* h, void* buf, int64_t cap, int64_t* bytes);
+rosko_status packed_deserialize(const void* buf, int64_t bytes, cudaStream_t st,
+                                rosko_packed_s** out);
 
 // selector.cu
 rosko_status select_learned(rosko_packed_s* h, int64_t N, rosko_tile* out, cudaStream_t st);

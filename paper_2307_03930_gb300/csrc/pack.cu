@@ -622,10 +622,10 @@ void plan_dense_tiles(rosko_packed_s* h, int32_t dense_min_pm) {
 }
 
 // Row-direct work segments (see rosko_packed_s) from the row-stream offsets,
-// at both granularities: {row, piece} in row order (nat) and, with a panel
-// order, in that order (ord).
+// at both granularities: {row, first record, end record, cut} in row order
+// (nat) and, with a panel order, in that order (ord).
 void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32_t>* panel_order,
-                   std::vector<int2> nat[2], std::vector<int2> ord[2]) {
+                   std::vector<int4> nat[2], std::vector<int4> ord[2]) {
   const int64_t M = h->M, P = h->P;
   const int64_t lens[2] = {kSegRecords, seg_records_for(h->nnz, M)};
   for (int g = 0; g < 2; ++g) {
@@ -641,7 +641,12 @@ void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32
         const int64_t nr = (int64_t)rp[r + 1] - rp[r] - 1;   // minus the sentinel
         const int64_t ns = std::max<int64_t>(1, (nr + seg - 1) / seg);
         if (ns > 1) panel_split[(size_t)p] = 1;
-        for (int64_t k = 0; k < ns; ++k) nat[g].push_back(make_int2((int)r, (int)k));
+        const int64_t row_end = (int64_t)rp[r + 1] - 1;
+        for (int64_t k = 0; k < ns; ++k) {
+          const int64_t e0 = (int64_t)rp[r] + k * seg;
+          nat[g].push_back(make_int4((int)r, (int)e0, (int)std::min<int64_t>(e0 + seg, row_end),
+                                     ns > 1 ? 1 : 0));
+        }
       }
     }
     panel_seg[(size_t)P] = (int64_t)nat[g].size();
@@ -797,7 +802,7 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
                                               (o_rp - o_sum64))
            : nullptr;
   if (dense) plan_dense_tiles(h, dense_min_pm);
-  std::vector<int2> nat[2], ord[2];
+  std::vector<int4> nat[2], ord[2];
   if (rows) plan_segments(h, rp, dense ? &h->panel_order_host : nullptr, nat, ord);
 
   const size_t rsz = rec_size(h->dt);
@@ -808,8 +813,8 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
   const size_t o_po = L.take(dense ? (size_t)P * 4 : 0);
   size_t o_seg[4];
   for (int g = 0; g < 2; ++g) {
-    o_seg[2 * g] = L.take(nat[g].size() * sizeof(int2));
-    o_seg[2 * g + 1] = L.take(ord[g].size() * sizeof(int2));
+    o_seg[2 * g] = L.take(nat[g].size() * sizeof(int4));
+    o_seg[2 * g + 1] = L.take(ord[g].size() * sizeof(int4));
   }
   const size_t staged = L.top;
   // written on the device
@@ -827,6 +832,7 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
   const size_t o_da =
       L.take(dense ? (size_t)h->n_copy * kDenseTileRows * (size_t)h->Kpad * 2 : 0, 1024);
   if (pool_malloc(&h->base, L.top + 256, st) != cudaSuccess) return ROSKO_ERR_OOM;
+  h->base_bytes = L.top + 256;
   char* b = static_cast<char*>(h->base);
   h->panel_col = reinterpret_cast<int32_t*>(b + o_pc);
   h->panel_nnz_dev = reinterpret_cast<int64_t*>(b + o_pn);
@@ -838,8 +844,8 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
     h->rowptr = reinterpret_cast<int32_t*>(b + o_rowptr);
     h->rnz = b + o_rnz;
     for (int g = 0; g < 2; ++g) {
-      h->segs[g].nat = reinterpret_cast<int2*>(b + o_seg[2 * g]);
-      h->segs[g].ord = dense ? reinterpret_cast<int2*>(b + o_seg[2 * g + 1]) : nullptr;
+      h->segs[g].nat = reinterpret_cast<int4*>(b + o_seg[2 * g]);
+      h->segs[g].ord = dense ? reinterpret_cast<int4*>(b + o_seg[2 * g + 1]) : nullptr;
     }
   }
   if (gather) {
@@ -860,9 +866,9 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
     }
     for (int g = 0; g < 2; ++g) {
       if (!nat[g].empty())
-        std::memcpy(stage.data() + o_seg[2 * g], nat[g].data(), nat[g].size() * sizeof(int2));
+        std::memcpy(stage.data() + o_seg[2 * g], nat[g].data(), nat[g].size() * sizeof(int4));
       if (!ord[g].empty())
-        std::memcpy(stage.data() + o_seg[2 * g + 1], ord[g].data(), ord[g].size() * sizeof(int2));
+        std::memcpy(stage.data() + o_seg[2 * g + 1], ord[g].data(), ord[g].size() * sizeof(int4));
     }
     // a pageable source is staged before the call returns
     if (cudaMemcpyAsync(b, stage.data(), staged, cudaMemcpyHostToDevice, st) != cudaSuccess)

@@ -327,44 +327,53 @@ constexpr int64_t kStaticRows = 1 << 20;   // largest M the static scratch serve
 static __device__ __align__(256) int32_t g_static_scratch[kStaticRows + 64];
 
 namespace {
-// Features from the integer statistics, on the device: the same definitions
-// as features_impl, evaluated in double and stored as FP32.
+// Features from the integer statistics, on the device, in FP32: the same
+// definitions as features_impl.  The counts are exact integers; each is
+// converted to FP32 once, and the ratios, square roots and logarithms are
+// FP32 operations (variances as mean of squares minus squared mean, so a
+// small coefficient of variation loses a few bits to cancellation).
 __global__ void features_finish_kernel(const unsigned long long* __restrict__ s, int64_t M,
                                        int64_t K, int64_t N, int64_t P, float* __restrict__ out) {
   if (threadIdx.x != 0) return;
-  double f[16];
-  const double Md = (double)M, Kd = (double)K, nnz = (double)s[0];
-  const double mean_row = M ? nnz / Md : 0.0;
-  f[0] = log2(Md);
-  f[1] = log2(Kd);
-  f[2] = log2((double)N);
-  f[3] = (M && K) ? nnz / (Md * Kd) : 0.0;
-  f[4] = log2(1.0 + nnz);
-  f[5] = log2(1.0 + mean_row);
-  const double var = M ? (double)s[1] / Md - mean_row * mean_row : 0.0;
-  f[6] = mean_row > 0 ? sqrt(fmax(var, 0.0)) / mean_row : 0.0;
-  f[7] = log2(1.0 + (double)s[2]) - log2(1.0 + mean_row);
-  for (int j = 0; j < 4; ++j) f[8 + j] = M ? (double)s[3 + j] / Md : 0.0;
-  const double Pd = (double)P;
-  f[12] = (P && K) ? (double)s[7] / (Pd * Kd) : 0.0;
-  const double mean_p = P ? nnz / Pd : 0.0;
-  const double var_p = P ? (double)s[8] / Pd - mean_p * mean_p : 0.0;
-  f[13] = mean_p > 0 ? sqrt(fmax(var_p, 0.0)) / mean_p : 0.0;
-  f[14] = log2(1.0 + (s[7] ? nnz / (double)s[7] : 0.0));
-  f[15] = P ? (double)s[9] / Pd : 0.0;
-  for (int j = 0; j < 16; ++j) out[j] = (float)f[j];
+  float f[16];
+  const float Mf = (float)M, Kf = (float)K, nnz = (float)s[0];
+  const float mean_row = M ? nnz / Mf : 0.0f;
+  f[0] = log2f(Mf);
+  f[1] = log2f(Kf);
+  f[2] = log2f((float)N);
+  f[3] = (M && K) ? (nnz / Mf) / Kf : 0.0f;
+  f[4] = log2f(1.0f + nnz);
+  f[5] = log2f(1.0f + mean_row);
+  const float var = M ? (float)s[1] / Mf - mean_row * mean_row : 0.0f;
+  f[6] = mean_row > 0.0f ? sqrtf(fmaxf(var, 0.0f)) / mean_row : 0.0f;
+  f[7] = log2f(1.0f + (float)s[2]) - log2f(1.0f + mean_row);
+  for (int j = 0; j < 4; ++j) f[8 + j] = M ? (float)s[3 + j] / Mf : 0.0f;
+  const float Pf = (float)P;
+  f[12] = (P && K) ? ((float)s[7] / Pf) / Kf : 0.0f;
+  const float mean_p = P ? nnz / Pf : 0.0f;
+  const float var_p = P ? (float)s[8] / Pf - mean_p * mean_p : 0.0f;
+  f[13] = mean_p > 0.0f ? sqrtf(fmaxf(var_p, 0.0f)) / mean_p : 0.0f;
+  f[14] = log2f(1.0f + (s[7] ? nnz / (float)s[7] : 0.0f));
+  f[15] = P ? (float)s[9] / Pf : 0.0f;
+  for (int j = 0; j < 16; ++j) out[j] = f[j];
 }
 }  // namespace
 
-// Device address of the static scratch, looked up once per device with that
-// device current (in host code the array's name is only a stand-in).
-static int32_t* static_scratch_address() {
+// Device address of the static scratch on the current device (in host code
+// the array's name is only a stand-in).  Looked up with that device current;
+// outside a stream capture the lookup is repeated on every call (a host-side
+// table lookup), so an address made stale by cudaDeviceReset is never used;
+// inside a capture the address cached by the device's last uncaptured call is
+// used, which is why the first call on a device must precede any capture.
+static int32_t* static_scratch_address(cudaStream_t st) {
   static int32_t* addr[64] = {nullptr};
   static std::mutex mu;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !addr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess) return nullptr;
     addr[dev] = static_cast<int32_t*>(p);
@@ -376,7 +385,7 @@ rosko_status features_static_impl(rosko_packed_s* h, int64_t N, float* features_
                                   cudaStream_t st) {
   const int64_t M = h->M, K = h->K, P = h->P;
   if (M > kStaticRows) return ROSKO_ERR_INVALID_ARG;
-  int32_t* base = static_scratch_address();
+  int32_t* base = static_scratch_address(st);
   if (!base) return ROSKO_ERR_CUDA;
   int32_t* rowcnt = base;
   auto* stats = reinterpret_cast<unsigned long long*>(base + kStaticRows);

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <cstdlib>
 
 #include "handle.hpp"
 
@@ -479,17 +480,34 @@ __global__ void __launch_bounds__(288, 1)
 // global memory (L2) instead of shared-memory slabs.  One warp owns one row
 // of C over a 32 V-column strip and walks that row's nonzeros (k ascending,
 // the same per-row order as the outer product of Alg. 2); each nonzero reads
-// its B row segment once.  With very sparse A a staged slab would hold rows
-// that few or none of the CTA's nonzeros use, while here every B byte read
-// is used and all of B (resident in the 129 MB L2) serves every SM.
-// A row's records are fetched 32 at a time across the lanes and broadcast
-// by shuffles in batches of four, whose B loads are all issued, into
-// registers of the storage type, before the FMAs.
+// its B row segment once.  With very sparse A a B row staged for a panel is
+// used by d*m_r << 1 rows of any panel whose C tile fits in registers, so a
+// staged slab would cost shared-memory bandwidth without saving L2 reads;
+// here every B byte read is used and all of B (resident in the 129 MB L2)
+// serves every SM.
+//
+// The traversal is bound by L2 and HBM latency, not arithmetic, so the
+// kernel is built to keep bytes in flight with few registers:
+//   * a work segment names its record range directly ({row, e0, e_end,
+//     cut}), so a warp reaches its B loads after two dependent loads (the
+//     segment, then 32 records fetched one per lane, coalesced);
+//   * records are broadcast by shuffles in groups of U; every lane copies its
+//     own column slice of each record's B row segment into its own slots of
+//     the warp's ring in shared memory (cp.async: the data in flight holds no
+//     register), two groups in flight, and reads back only what it copied
+//     (no barrier: each lane waits for its own copies);
+//   * BF16 uses the mixed-precision FMA (BF16 x BF16 + FP32 -> FP32, one
+//     rounding: the exact product added to the FP32 sum), which needs no
+//     conversion instructions (measured on GB300: 58 against 35 MACs per
+//     clock per SM for convert + FP32 FMA).
+// Measured on the 512 x 4608 x 3136 layer (BF16): register-held batches of
+// B loads reached 29 us at 99% sparsity (16 resident warps per SM, latency
+// bound), this ring 19 us (24 warps per SM, twice the bytes in flight).
 //
 // One launch serves a batch: the problems travel in the kernel parameters
-// and the blocks of problem q are [blocks0(q), blocks0(q+1)); a block is 8
-// rows x one strip, strips fastest so that neighbouring blocks share the
-// rows' records.
+// and the items of problem q are [items0(q), items0(q+1)); an item is one
+// segment x one strip, strips fastest so that neighbouring warps share the
+// segment's records; a block is 8 items.
 // Warp broadcast of one nonzero record from lane `src`.
 __device__ __forceinline__ uint32_t shfl_rec(uint32_t w, int src) {
   return __shfl_sync(0xffffffffu, w, src);
@@ -511,25 +529,71 @@ template <> struct RawOf<4> { using type = uint32_t; };
 template <> struct RawOf<8> { using type = uint2; };
 template <> struct RawOf<16> { using type = uint4; };
 
+// c0 += a * lo(b), c1 += a * hi(b): a is the BF16 value in the high half of
+// the record word, b two BF16 values of B; one rounding each.
+__device__ __forceinline__ void fma_bf16x2(float& c0, float& c1, uint32_t rec, uint32_t b) {
+  asm("{\n\t.reg .b16 al, ah, bl, bh;\n\t"
+      "mov.b32 {al, ah}, %2;\n\t"
+      "mov.b32 {bl, bh}, %3;\n\t"
+      "fma.rn.f32.bf16 %0, ah, bl, %0;\n\t"
+      "fma.rn.f32.bf16 %1, ah, bh, %1;\n\t}"
+      : "+f"(c0), "+f"(c1)
+      : "r"(rec), "r"(b));
+}
+
 struct DirectProb {
-  const int32_t* rowptr;      // row stream: per-row k-ascending records + sentinel
-  const void* rnz;
-  const int2* segs;           // work segments {row, piece}
+  const void* rnz;            // row stream: per-row k-ascending records + sentinel
+  const int4* segs;           // work segments {row, e0, e_end, cut}
   const float* row_scale;     // INT8 dequantisation
   const float* col_scale;
   const void* B;
   void* C;
   int64_t n_segs, ldb, ldc, M, N;
-  int64_t blocks0;            // first block of this problem
+  int64_t items0;             // first work item of this problem
   int strips, load_c_first, add_c_at_end, vec_ok;
-  int seg_records;            // nonzeros per piece of a cut row
 };
 
 template <int NP>
 struct DirectTable {
   DirectProb p[NP];
+  int64_t total;              // work items of all problems
   int count;
 };
+
+// Asynchronous copy of `bytes` (8 or 16) global -> shared, zero-filling
+// past the first `src_bytes` (which may be 0: nothing is read).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int src_bytes) {
+  if constexpr (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(BYTES),
+                 "r"(src_bytes)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The warp's ring: two groups of U records; group g + 1 is in flight while
+// group g is multiplied, then group g + 2 takes g's slots.  U = 8 records of
+// 16 bytes per lane (4 when a lane's slice is 32 bytes, or with FP64
+// accumulators): 8 KB of ring per warp, three 8-warp blocks per SM.
+template <class TA, class TB, class TC, int V, int NP>
+constexpr int async_batch() {
+  return ((V * (int)sizeof(TB)) >= 32 || std::is_same<TA, double>::value) ? 4 : 8;
+}
+template <class TA, class TB, class TC, int V, int NP>
+constexpr size_t async_smem_bytes() {
+  return (size_t)8 * 2 * async_batch<TA, TB, TC, V, NP>() * 32 * V * sizeof(TB);
+}
 
 template <class TA, class TB, class TC, int V, int NP>
 __global__ void __launch_bounds__(256, 3)
@@ -537,73 +601,51 @@ __global__ void __launch_bounds__(256, 3)
   using TACC = typename AccOf<TA>::type;
   using WT = typename RowRec<TA>::T;
   constexpr int G = (16 / (int)sizeof(TB)) < 8 ? (16 / (int)sizeof(TB)) : 8;
-  constexpr int CE = V < G ? V : G;   // elements per lane chunk (<= 16 bytes)
+  constexpr int CE = V < G ? V : G;   // elements per lane chunk (8 or 16 bytes)
   constexpr int J = V / CE;           // chunks per lane, 32 CE columns apart
-  // records in flight per warp (batches of eight measured slower for every
-  // B type)
-  constexpr int U = 4;
+  constexpr int CB = CE * (int)sizeof(TB);   // bytes per chunk
+  constexpr int U = async_batch<TA, TB, TC, V, NP>();
   static_assert(J * CE == V, "V must be a multiple of the chunk width");
+  static_assert(CB == 8 || CB == 16, "chunks of 8 or 16 bytes");
+  static_assert(32 % U == 0, "groups must tile the 32 records of a fetch");
   constexpr bool kDp4a = std::is_same<TB, int8_t>::value && std::is_same<TACC, int32_t>::value &&
-                         U == 4 && CE == 8 && J == 1;
+                         U % 4 == 0 && CE == 8 && J == 1;
+  constexpr bool kMixed = std::is_same<TA, __nv_bfloat16>::value &&
+                          std::is_same<TB, __nv_bfloat16>::value && CE % 2 == 0;
+  using RawT = typename RawOf<CB>::type;
+  extern __shared__ __align__(16) unsigned char ring_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t it = (int64_t)blockIdx.x * 8 + warp;
+  if (it >= T.total) return;
+  // this warp's ring: [2 groups][U records][J chunks][32 lanes] of CB bytes
+  const uint32_t ring = smem_u32(ring_smem) + (uint32_t)(warp * 2 * U * J * 32 * CB);
+  const unsigned char* ring_gen = ring_smem + (size_t)warp * 2 * U * J * 32 * CB;
   int q = 0;
-  while (q + 1 < T.count && (int64_t)blockIdx.x >= T.p[q + 1].blocks0) ++q;
+  while (q + 1 < T.count && it >= T.p[q + 1].items0) ++q;
   const DirectProb& P = T.p[q];
-  const int64_t lb = (int64_t)blockIdx.x - P.blocks0;
-  const int64_t strip = lb % P.strips;
-  const int64_t w = (lb / P.strips) * 8 + warp;
-  if (w >= P.n_segs) return;
-  // this warp's segment: piece `seg.y` (at most seg_records nonzeros) of row
-  // `seg.x`; the pieces of a cut row are added into C atomically
-  const int2 seg = __ldg(&P.segs[w]);
+  const int64_t local = it - P.items0;
+  const int64_t si = local / P.strips;
+  const int64_t strip = local - si * P.strips;
+  const int4 seg = __ldg(&P.segs[si]);
   const int64_t row = seg.x;
+  const int e0 = seg.y, e_end = seg.z;
+  const bool cut = seg.w != 0;
   const int64_t n0 = strip * (32 * V);
+  const int64_t N = P.N, ldb = P.ldb;
   TACC acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = TACC(0);
   TC* crow = reinterpret_cast<TC*>(P.C) + row * P.ldc;
-  // which of this lane's chunks lie wholly inside N (the others load scalars)
-  bool whole[J];
-#pragma unroll
-  for (int j = 0; j < J; ++j) whole[j] = n0 + j * 32 * CE + lane * CE + CE <= P.N;
   const WT* __restrict__ rnz = reinterpret_cast<const WT*>(P.rnz);
-  const int r0 = __ldg(&P.rowptr[row]);
-  const int r_end = __ldg(&P.rowptr[row + 1]) - 1;   // the last record is the sentinel
-  const bool cut = r_end - r0 > P.seg_records;
-  const int e0 = r0 + seg.y * P.seg_records;
-  const int e_end = min(e0 + P.seg_records, r_end);
-  const TB* bcol = static_cast<const TB*>(P.B) + n0 + lane * CE;
-  const int64_t ldb = P.ldb, N = P.N;
-  // B chunks stay in their storage type until the FMAs (BF16 / INT8 take
-  // half / a quarter of the registers of their accumulator type), so more
-  // records' loads are in flight per warp
-  using RawT = typename RawOf<CE * (int)sizeof(TB)>::type;
-  auto load_raw = [&](int k, RawT* raw) {
-    const TB* src = bcol + (int64_t)k * ldb;
+  const TB* Bbase = static_cast<const TB*>(P.B);
+  // bytes of each of this lane's chunks inside N (0: past the end)
+  int valid[J];
 #pragma unroll
-    for (int jj = 0; jj < J; ++jj) {
-      if (whole[jj]) {
-        raw[jj] = *reinterpret_cast<const RawT*>(src + jj * 32 * CE);
-      } else {
-        TB tmp[CE];
-#pragma unroll
-        for (int v = 0; v < CE; ++v) {
-          const int64_t col = n0 + jj * 32 * CE + lane * CE + v;
-          tmp[v] = col < N ? src[jj * 32 * CE + v] : TB(0);
-        }
-        raw[jj] = *reinterpret_cast<const RawT*>(tmp);
-      }
-    }
-  };
-  auto fma_raw = [&](TACC a, const RawT* raw) {
-#pragma unroll
-    for (int jj = 0; jj < J; ++jj) {
-      const TB* vals = reinterpret_cast<const TB*>(&raw[jj]);
-#pragma unroll
-      for (int v = 0; v < CE; ++v)
-        acc[jj * CE + v] = mac(a, to_acc(vals[v], TACC(0)), acc[jj * CE + v]);
-    }
-  };
+  for (int jj = 0; jj < J; ++jj) {
+    const int64_t col = n0 + jj * 32 * CE + lane * CE;
+    const int64_t left = N - col;
+    valid[jj] = left <= 0 ? 0 : (left >= CE ? CB : (int)left * (int)sizeof(TB));
+  }
   if (P.load_c_first && !cut) {
 #pragma unroll
     for (int jj = 0; jj < J; ++jj)
@@ -613,57 +655,110 @@ __global__ void __launch_bounds__(256, 3)
         if (col < N) acc[jj * CE + v] = (TACC)crow[col];
       }
   }
-  // 32 records at a time: lane i loads record i (one coalesced request),
-  // then batches of U are broadcast by shuffles and their B loads issued
-  // together, so a row costs few dependent round trips to memory
-  for (int base = e0; base < e_end; base += 32) {
-    const int cnt = min(32, e_end - base);
-    WT mine;
-    if (lane < cnt) mine = rnz[base + lane];
-    else mine = rnz[e_end];               // the sentinel: never used
-    for (int t = 0; t < cnt; t += U) {
-      WT w[U];
-      RawT raw[U][J];
+  auto slot_off = [&](int grp, int u, int jj) -> uint32_t {
+    return (uint32_t)((((grp * U + u) * J + jj) * 32 + lane) * CB);
+  };
+  // issue group `grp` (records t .. t+U-1 of the fetch held in `m`)
+  auto issue = [&](WT m, int cnt, int t, int grp, WT (&wb)[U]) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) w[u] = shfl_rec(mine, t + u < cnt ? t + u : t);
+    for (int u = 0; u < U; ++u) wb[u] = shfl_rec(m, t + u);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (t + u < cnt) {
-          load_raw(RowRec<TA>::k(w[u]), raw[u]);
-        } else {
+    for (int u = 0; u < U; ++u) {
+      if (t + u < cnt) {
+        const TB* src = Bbase + (int64_t)RowRec<TA>::k(wb[u]) * ldb + n0 + lane * CE;
 #pragma unroll
-          for (int jj = 0; jj < J; ++jj) raw[u][jj] = RawT{};
-        }
+        for (int jj = 0; jj < J; ++jj)
+          cp_async<CB>(ring + slot_off(grp, u, jj), valid[jj] ? (const void*)(src + jj * 32 * CE)
+                                                             : (const void*)Bbase,
+                       valid[jj]);
       }
-      if constexpr (kDp4a) {
-        // INT8: the four records' B rows (eight INT8 columns per lane each)
-        // are transposed by byte permutes into one 4-byte word per column
-        // (the four rows' bytes) and multiplied with the four A codes by one
-        // 4-way byte dot product per column - exact, like the IMAD chain
+    }
+    cp_async_commit();
+  };
+  auto consume = [&](int cnt, int t, int grp, const WT (&wb)[U]) {
+    RawT rb[U][J];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int jj = 0; jj < J; ++jj)
+        rb[u][jj] = *reinterpret_cast<const RawT*>(ring_gen + slot_off(grp, u, jj));
+    if constexpr (kDp4a) {
+#pragma unroll
+      for (int g4 = 0; g4 < U / 4; ++g4) {
         uint32_t ap = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          ap |= (t + u < cnt ? ((uint32_t)w[u] >> 16) & 0xFFu : 0u) << (8 * u);
+        for (int u = 0; u < 4; ++u)
+          ap |= (t + 4 * g4 + u < cnt ? ((uint32_t)wb[4 * g4 + u] >> 16) & 0xFFu : 0u) << (8 * u);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const uint32_t q0 = h ? raw[0][0].y : raw[0][0].x;
-          const uint32_t q1 = h ? raw[1][0].y : raw[1][0].x;
-          const uint32_t q2 = h ? raw[2][0].y : raw[2][0].x;
-          const uint32_t q3 = h ? raw[3][0].y : raw[3][0].x;
-          const uint32_t lo01 = __byte_perm(q0, q1, 0x5140);   // q0.b0 q1.b0 q0.b1 q1.b1
+          const uint32_t q0 = h ? rb[4 * g4 + 0][0].y : rb[4 * g4 + 0][0].x;
+          const uint32_t q1 = h ? rb[4 * g4 + 1][0].y : rb[4 * g4 + 1][0].x;
+          const uint32_t q2 = h ? rb[4 * g4 + 2][0].y : rb[4 * g4 + 2][0].x;
+          const uint32_t q3 = h ? rb[4 * g4 + 3][0].y : rb[4 * g4 + 3][0].x;
+          const uint32_t lo01 = __byte_perm(q0, q1, 0x5140);
           const uint32_t lo23 = __byte_perm(q2, q3, 0x5140);
-          const uint32_t hi01 = __byte_perm(q0, q1, 0x7362);   // q0.b2 q1.b2 q0.b3 q1.b3
+          const uint32_t hi01 = __byte_perm(q0, q1, 0x7362);
           const uint32_t hi23 = __byte_perm(q2, q3, 0x7362);
+          // a slot past the fetch holds stale bytes: its code in ap is 0
           acc[4 * h + 0] = __dp4a((int)__byte_perm(lo01, lo23, 0x5410), (int)ap, acc[4 * h + 0]);
           acc[4 * h + 1] = __dp4a((int)__byte_perm(lo01, lo23, 0x7632), (int)ap, acc[4 * h + 1]);
           acc[4 * h + 2] = __dp4a((int)__byte_perm(hi01, hi23, 0x5410), (int)ap, acc[4 * h + 2]);
           acc[4 * h + 3] = __dp4a((int)__byte_perm(hi01, hi23, 0x7632), (int)ap, acc[4 * h + 3]);
         }
-      } else {
+      }
+    } else {
 #pragma unroll
-        for (int u = 0; u < U; ++u) fma_raw(t + u < cnt ? RowRec<TA>::a(w[u]) : TACC(0), raw[u]);
+      for (int u = 0; u < U; ++u) {
+        if (t + u >= cnt) continue;
+        if constexpr (kMixed) {
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) {
+            const uint32_t* wds = reinterpret_cast<const uint32_t*>(&rb[u][jj]);
+#pragma unroll
+            for (int h = 0; h < CE / 2; ++h)
+              fma_bf16x2(acc[jj * CE + 2 * h], acc[jj * CE + 2 * h + 1], (uint32_t)wb[u], wds[h]);
+          }
+        } else {
+          const TACC a = RowRec<TA>::a(wb[u]);
+#pragma unroll
+          for (int jj = 0; jj < J; ++jj) {
+            const TB* vals = reinterpret_cast<const TB*>(&rb[u][jj]);
+#pragma unroll
+            for (int v = 0; v < CE; ++v)
+              acc[jj * CE + v] = mac(a, to_acc(vals[v], TACC(0)), acc[jj * CE + v]);
+          }
+        }
       }
     }
+  };
+  // 32 records per fetch (lane i holds record i; the next fetch of the row is
+  // issued before this one is consumed); groups of U alternate between the
+  // two halves of the ring
+  WT mine = lane < e_end - e0 ? rnz[e0 + lane] : rnz[e_end];   // e_end: sentinel or record
+  for (int base = e0; base < e_end; base += 32) {
+    const int cnt = min(32, e_end - base);
+    WT nmine = mine;
+    if (base + 32 < e_end) nmine = base + 32 + lane < e_end ? rnz[base + 32 + lane] : rnz[e_end];
+    WT wa[U], wbb[U];
+    issue(mine, cnt, 0, 0, wa);
+    for (int t = 0; t < cnt; t += 2 * U) {
+      if (t + U < cnt) {
+        issue(mine, cnt, t + U, 1, wbb);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      consume(cnt, t, 0, wa);
+      if (t + U >= cnt) break;
+      if (t + 2 * U < cnt) {
+        issue(mine, cnt, t + 2 * U, 0, wa);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      consume(cnt, t + U, 1, wbb);
+    }
+    mine = nmine;
   }
   // C written once (dequantisation needs the scales of this problem)
   SparseParams sp{};
@@ -675,8 +770,6 @@ __global__ void __launch_bounds__(256, 3)
     if (col0 >= N) continue;
     TC o[CE];
     if (cut) {
-      // a piece of a cut row: add into C (zeroed before the launch unless
-      // the call accumulates)
 #pragma unroll
       for (int v = 0; v < CE; ++v)
         if (col0 + v < N)
@@ -755,21 +848,26 @@ Entry g_table[] = {
     ROSKO_GATHER(double, float, double, ROSKO_F64, ROSKO_F32, ROSKO_F64, 16, 2),
 };
 
+// Row-direct variants: V columns per lane (one 16-byte chunk for BF16 at
+// V = 8), the shared-memory ring sized per variant.
 struct DirectEntry {
   rosko_dtype a, b, c;
   int V;
   void (*one)(const DirectTable<1>);
   void (*many)(const DirectTable<64>);
+  size_t smem;                   // dynamic shared memory (the warps' rings)
+  mutable bool attr_set = false;
 };
 
-#define ROSKO_DIRECT(TA, TB, TC, DA, DB, DC, V) \
-  {DA, DB, DC, V, rowdirect_kernel<TA, TB, TC, V, 1>, rowdirect_kernel<TA, TB, TC, V, 64>}
+#define ROSKO_DIRECT(TA, TB, TC, DA, DB, DC, V)                                              \
+  {DA, DB, DC, V, rowdirect_kernel<TA, TB, TC, V, 1>, rowdirect_kernel<TA, TB, TC, V, 64>, \
+   async_smem_bytes<TA, TB, TC, V, 1>()}
 
-// Row-direct: V columns per lane (one 16-byte chunk for BF16 at V = 8).
 const DirectEntry g_direct[] = {
-    ROSKO_DIRECT(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 4),
     ROSKO_DIRECT(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 8),
+    ROSKO_DIRECT(float, float, float, ROSKO_F32, ROSKO_F32, ROSKO_F32, 4),
     ROSKO_DIRECT(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 8),
+    ROSKO_DIRECT(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 16),
     ROSKO_DIRECT(__nv_bfloat16, __nv_bfloat16, float, ROSKO_BF16, ROSKO_BF16, ROSKO_F32, 4),
     ROSKO_DIRECT(int8_t, int8_t, int32_t, ROSKO_I8, ROSKO_I8, ROSKO_I32, 8),
     ROSKO_DIRECT(int8_t, int8_t, float, ROSKO_I8, ROSKO_I8, ROSKO_F32, 8),
@@ -822,13 +920,13 @@ int sparse_default_V(rosko_dtype p_dt, int R, int order) {
 // handle's panel_order with n_panels its first entries); *n_segs receives
 // their count, *cut whether one of those rows is cut into several pieces.
 // NULL for a list of another kind.
-const int2* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
+const int4* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
                             int which, int64_t* n_segs, bool* cut) {
   if (cut) *cut = false;
   *n_segs = -1;
   const rosko_packed_s::SegList& L = h->segs[which & 1];
   if (!L.nat || n_panels < 0 || n_panels > h->P) return nullptr;
-  const int2* base;
+  const int4* base;
   if (!panel_list) {
     // all panels in order (the prefix sums' last entry is the total in
     // either order)
@@ -857,17 +955,16 @@ int direct_pick(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_pa
 
 // Fill one problem of a row-direct table; returns the problem's block count
 // (< 0: invalid argument).
-static int64_t direct_prob(const DirectJob& j, int V, int64_t blocks0, DirectProb* P) {
+static int64_t direct_prob(const DirectJob& j, int V, int64_t items0, DirectProb* P) {
   const rosko_packed_s* h = j.h;
   const size_t bsz = dtype_size(j.b_dt), csz = dtype_size(j.c_dt);
   // 16-byte lane loads: B rows must start on 16-byte boundaries
   if (reinterpret_cast<uintptr_t>(j.B) % 16 != 0 || (j.ldb * (int64_t)bsz) % 16 != 0) return -1;
   int64_t n_segs = 0;
   const int which = direct_pick(h, j.panel_list, j.n_panels, j.N, V);
-  const int2* segs = direct_segments(h, j.panel_list, j.n_panels, which, &n_segs, nullptr);
+  const int4* segs = direct_segments(h, j.panel_list, j.n_panels, which, &n_segs, nullptr);
   if (!segs) return -1;
   std::memset(P, 0, sizeof(*P));
-  P->rowptr = h->rowptr;
   P->rnz = h->rnz;
   P->segs = segs;
   P->row_scale = h->row_scale;
@@ -880,13 +977,12 @@ static int64_t direct_prob(const DirectJob& j, int V, int64_t blocks0, DirectPro
   P->M = h->M;
   P->N = j.N;
   P->strips = (int)((j.N + 32 * V - 1) / (32 * V));
-  P->seg_records = h->segs[which].records;
   const bool dequant = (h->dt == ROSKO_I8 && j.c_dt == ROSKO_F32);
   P->load_c_first = j.accumulate && !dequant;
   P->add_c_at_end = j.accumulate && dequant;
   P->vec_ok = ((reinterpret_cast<uintptr_t>(j.C) % 16) == 0) && ((j.ldc * (int64_t)csz) % 16 == 0);
-  P->blocks0 = blocks0;
-  return ((n_segs + 7) / 8) * P->strips;
+  P->items0 = items0;
+  return n_segs * P->strips;
 }
 
 rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaStream_t st) {
@@ -900,33 +996,42 @@ rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaSt
   const DirectEntry* e = find_direct(a, b, c, V);
   if (!e) return ROSKO_ERR_UNSUPPORTED;
   auto fill = [&](auto& T) -> int64_t {
-    int64_t blocks = 0;
+    int64_t items = 0;
     int n = 0;
     for (int i = 0; i < count; ++i) {
       if (jobs[i].N <= 0 || jobs[i].n_panels <= 0) continue;
-      const int64_t nb = direct_prob(jobs[i], V, blocks, &T.p[n]);
-      if (nb < 0) return -1;
-      if (nb == 0) continue;
-      blocks += nb;
+      const int64_t ni = direct_prob(jobs[i], V, items, &T.p[n]);
+      if (ni < 0) return -1;
+      if (ni == 0) continue;
+      items += ni;
       ++n;
     }
     T.count = n;
-    return blocks;
+    T.total = items;
+    return items;
   };
+  if (!e->attr_set) {
+    if (cudaFuncSetAttribute(e->one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(e->many, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem) !=
+            cudaSuccess)
+      return ROSKO_ERR_CUDA;
+    e->attr_set = true;
+  }
   if (count == 1) {
     DirectTable<1> T;
     std::memset(static_cast<void*>(&T), 0, sizeof(T));
-    const int64_t blocks = fill(T);
-    if (blocks < 0 || blocks > INT_MAX) return ROSKO_ERR_INVALID_ARG;
-    if (blocks == 0) return ROSKO_OK;
-    e->one<<<(unsigned)blocks, 256, 0, st>>>(T);
+    const int64_t items = fill(T);
+    if (items < 0 || (items + 7) / 8 > INT_MAX) return ROSKO_ERR_INVALID_ARG;
+    if (items == 0) return ROSKO_OK;
+    e->one<<<(unsigned)((items + 7) / 8), 256, e->smem, st>>>(T);
   } else {
     DirectTable<64> T;
     std::memset(static_cast<void*>(&T), 0, sizeof(T));
-    const int64_t blocks = fill(T);
-    if (blocks < 0 || blocks > INT_MAX) return ROSKO_ERR_INVALID_ARG;
-    if (blocks == 0) return ROSKO_OK;
-    e->many<<<(unsigned)blocks, 256, 0, st>>>(T);
+    const int64_t items = fill(T);
+    if (items < 0 || (items + 7) / 8 > INT_MAX) return ROSKO_ERR_INVALID_ARG;
+    if (items == 0) return ROSKO_OK;
+    e->many<<<(unsigned)((items + 7) / 8), 256, e->smem, st>>>(T);
   }
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;

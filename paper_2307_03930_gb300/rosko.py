@@ -91,6 +91,12 @@ def lib() -> ctypes.CDLL:
         "rosko_schedule_analytic": (ci, [i64, i64, i64, i64, i32, ci, P_tile]),
         "rosko_device_status": (ci, [ctypes.POINTER(i32), ci]),
         "rosko_kernel_launches": (i64, []),
+        "rosko_set_wait_limit": (ci, [i64]),
+        "rosko_pack_save": (ci, [vp, vp, i64, ctypes.POINTER(i64)]),
+        "rosko_packed_shape": (ci, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                    ctypes.POINTER(i64)]),
+        "rosko_pack_load": (ci, [vp, i64, vp, ctypes.POINTER(vp)]),
+        "rosko_probe_bounded_wait": (ci, [vp]),
         "rosko_num_candidates": (i32, []),
         "rosko_candidate": (ci, [vp, i64, i32, P_tile]),
         "rosko_autotune": (ci, [vp, vp, ci, i64, i64, vp, vp, ci, i64, i32, P_tile,
@@ -259,9 +265,13 @@ def rosko_packed_info(A: PackedA) -> dict:
                                  ctypes.byref(i64[2]), ctypes.byref(i64[3]),
                                  ctypes.byref(m_r), ctypes.byref(dt), ctypes.byref(i64[4]))
     _check(st, "rosko_packed_info")
+    M, K, dev_bytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().rosko_packed_shape(A.handle, ctypes.byref(M), ctypes.byref(K),
+                                    ctypes.byref(dev_bytes)), "rosko_packed_shape")
     return {"nnz": i64[0].value, "bytes": i64[1].value, "touched_k": i64[2].value,
             "n_panels": i64[3].value, "m_r": m_r.value, "dtype": dt.value,
-            "n_cols": i64[4].value}
+            "n_cols": i64[4].value, "M": M.value, "K": K.value,
+            "device_bytes": dev_bytes.value}
 
 
 def rosko_packed_export(A: PackedA) -> dict:
@@ -316,6 +326,40 @@ def rosko_device_status(clear: bool = False) -> int:
 
 def rosko_kernel_launches() -> int:
     return int(lib().rosko_kernel_launches())
+
+
+def rosko_pack_save(A: PackedA) -> bytes:
+    """Byte image of a packed handle (rosko_pack_load restores it)."""
+    L = lib()
+    n = ctypes.c_int64()
+    _check(L.rosko_pack_save(A.handle, None, 0, ctypes.byref(n)), "rosko_pack_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(L.rosko_pack_save(A.handle, buf, n.value, ctypes.byref(n)), "rosko_pack_save")
+    return buf.raw[: n.value]
+
+
+def rosko_pack_load(image: bytes, stream=None) -> PackedA:
+    """A new handle on the current device from a rosko_pack_save image."""
+    L = lib()
+    out = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(bytes(image), len(image))
+    _check(L.rosko_pack_load(buf, len(image), ctypes.c_void_p(_stream(stream)), ctypes.byref(out)),
+           "rosko_pack_load")
+    h = PackedA(out.value, 0, 0)
+    i = rosko_packed_info(h)
+    h.M, h.K = i["M"], i["K"]
+    return h
+
+
+def rosko_set_wait_limit(ns: int) -> None:
+    """Bounded-wait limit of the current device in ns (0: the 2 s default)."""
+    _check(lib().rosko_set_wait_limit(int(ns)), "rosko_set_wait_limit")
+
+
+def rosko_probe_bounded_wait(stream=None) -> None:
+    """Launch the failure-detection probe (a wait that runs out)."""
+    _check(lib().rosko_probe_bounded_wait(ctypes.c_void_p(_stream(stream))),
+           "rosko_probe_bounded_wait")
 
 
 def rosko_num_candidates() -> int:

@@ -177,6 +177,9 @@ rosko_status rosko_pack_transposed(const void* A_dev, rosko_dtype a_dtype, int64
  * differ run to run in the last bits.  N may be 0 (no-op).
  * Dense-panel tiles (BF16) multiply their explicit zeros too, so there a
  * non-finite B value meets 0 * Inf = NaN, while skipped rows never see it.
+ * The row-direct traversal numbers its work items (row pieces x column
+ * strips of n_r columns) with 31 bits; beyond that it returns
+ * ROSKO_ERR_UNSUPPORTED.
  */
 rosko_status rosko_spmm(rosko_packed_t A, const void* B_dev, rosko_dtype b_dtype, int64_t N,
                         int64_t ldb, const float* col_scale_dev, void* C_dev,

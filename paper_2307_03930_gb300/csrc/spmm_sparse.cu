@@ -574,6 +574,53 @@ __device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int src_
                  : "memory");
   }
 }
+// Same, with an L2 eviction policy (createpolicy) for the line.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_hint(uint32_t dst, const void* src, int src_bytes,
+                                              uint64_t policy) {
+  if constexpr (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(dst),
+                 "l"(src), "r"(src_bytes), "l"(policy)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3, %4;" ::"r"(dst),
+                 "l"(src), "n"(BYTES), "r"(src_bytes), "l"(policy)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Loads of the handle's small arrays (segments, records) that should stay in
+// L2 across launches while B streams through it.
+__device__ __forceinline__ int4 ld_keep(const int4* p, uint64_t pol) {
+  int4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_keep(const uint2* p, uint64_t pol) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ RecF64 ld_keep(const RecF64* p, uint64_t) { return *p; }
+
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -615,36 +662,42 @@ __global__ void __launch_bounds__(256, 3)
   using RawT = typename RawOf<CB>::type;
   extern __shared__ __align__(16) unsigned char ring_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t it = (int64_t)blockIdx.x * 8 + warp;
-  if (it >= T.total) return;
+  // the host launches at most 2^31 - 1 items
+  const int it = (int)blockIdx.x * 8 + warp;
+  if (it >= (int)T.total) return;
+  const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
   // this warp's ring: [2 groups][U records][J chunks][32 lanes] of CB bytes
   const uint32_t ring = smem_u32(ring_smem) + (uint32_t)(warp * 2 * U * J * 32 * CB);
   const unsigned char* ring_gen = ring_smem + (size_t)warp * 2 * U * J * 32 * CB;
   int q = 0;
-  while (q + 1 < T.count && it >= T.p[q + 1].items0) ++q;
+  while (q + 1 < T.count && (int64_t)it >= T.p[q + 1].items0) ++q;
   const DirectProb& P = T.p[q];
-  const int64_t local = it - P.items0;
-  const int64_t si = local / P.strips;
-  const int64_t strip = local - si * P.strips;
-  const int4 seg = __ldg(&P.segs[si]);
+  const int local = it - (int)P.items0;
+  const int si = local / P.strips;
+  const int strip = local - si * P.strips;
+  const int4 seg = ld_keep(&P.segs[si], keep);
   const int64_t row = seg.x;
   const int e0 = seg.y, e_end = seg.z;
   const bool cut = seg.w != 0;
-  const int64_t n0 = strip * (32 * V);
-  const int64_t N = P.N, ldb = P.ldb;
+  const int64_t n0 = (int64_t)strip * (32 * V);
+  const int64_t N = P.N;
   TACC acc[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) acc[v] = TACC(0);
   TC* crow = reinterpret_cast<TC*>(P.C) + row * P.ldc;
   const WT* __restrict__ rnz = reinterpret_cast<const WT*>(P.rnz);
-  const TB* Bbase = static_cast<const TB*>(P.B);
-  // bytes of each of this lane's chunks inside N (0: past the end)
+  // per lane chunk: the bytes inside N (0: past the end) and the chunk's
+  // address in row 0 of B (column 0 when nothing is read), so that a
+  // record's copy source is one multiply-add away
   int valid[J];
+  const char* lane_ptr[J];
+  const int64_t row_bytes = P.ldb * (int64_t)sizeof(TB);
 #pragma unroll
   for (int jj = 0; jj < J; ++jj) {
     const int64_t col = n0 + jj * 32 * CE + lane * CE;
     const int64_t left = N - col;
     valid[jj] = left <= 0 ? 0 : (left >= CE ? CB : (int)left * (int)sizeof(TB));
+    lane_ptr[jj] = static_cast<const char*>(P.B) + (valid[jj] ? col * (int64_t)sizeof(TB) : 0);
   }
   if (P.load_c_first && !cut) {
 #pragma unroll
@@ -658,19 +711,19 @@ __global__ void __launch_bounds__(256, 3)
   auto slot_off = [&](int grp, int u, int jj) -> uint32_t {
     return (uint32_t)((((grp * U + u) * J + jj) * 32 + lane) * CB);
   };
-  // issue group `grp` (records t .. t+U-1 of the fetch held in `m`)
+  // issue group `grp` (records t .. t+U-1 of the fetch held in `m`); B rows
+  // stream through L2 (evict first)
   auto issue = [&](WT m, int cnt, int t, int grp, WT (&wb)[U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) wb[u] = shfl_rec(m, t + u);
+    const bool full = cnt - t >= U;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (t + u < cnt) {
-        const TB* src = Bbase + (int64_t)RowRec<TA>::k(wb[u]) * ldb + n0 + lane * CE;
+      if (full || t + u < cnt) {
+        const int64_t off = (int64_t)(uint32_t)RowRec<TA>::k(wb[u]) * row_bytes;
 #pragma unroll
         for (int jj = 0; jj < J; ++jj)
-          cp_async<CB>(ring + slot_off(grp, u, jj), valid[jj] ? (const void*)(src + jj * 32 * CE)
-                                                             : (const void*)Bbase,
-                       valid[jj]);
+          cp_async_hint<CB>(ring + slot_off(grp, u, jj), lane_ptr[jj] + off, valid[jj], stream);
       }
     }
     cp_async_commit();
@@ -707,9 +760,10 @@ __global__ void __launch_bounds__(256, 3)
         }
       }
     } else {
+      const bool full = cnt - t >= U;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (t + u >= cnt) continue;
+        if (!full && t + u >= cnt) continue;
         if constexpr (kMixed) {
 #pragma unroll
           for (int jj = 0; jj < J; ++jj) {
@@ -734,11 +788,14 @@ __global__ void __launch_bounds__(256, 3)
   // 32 records per fetch (lane i holds record i; the next fetch of the row is
   // issued before this one is consumed); groups of U alternate between the
   // two halves of the ring
-  WT mine = lane < e_end - e0 ? rnz[e0 + lane] : rnz[e_end];   // e_end: sentinel or record
+  // records stay in L2 across launches (evict last): e_end is the row's
+  // sentinel or the next piece's first record, always inside the stream
+  WT mine = ld_keep(&rnz[lane < e_end - e0 ? e0 + lane : e_end], keep);
   for (int base = e0; base < e_end; base += 32) {
     const int cnt = min(32, e_end - base);
     WT nmine = mine;
-    if (base + 32 < e_end) nmine = base + 32 + lane < e_end ? rnz[base + 32 + lane] : rnz[e_end];
+    if (base + 32 < e_end)
+      nmine = ld_keep(&rnz[base + 32 + lane < e_end ? base + 32 + lane : e_end], keep);
     WT wa[U], wbb[U];
     issue(mine, cnt, 0, 0, wa);
     for (int t = 0; t < cnt; t += 2 * U) {
@@ -1022,14 +1079,14 @@ rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaSt
     DirectTable<1> T;
     std::memset(static_cast<void*>(&T), 0, sizeof(T));
     const int64_t items = fill(T);
-    if (items < 0 || (items + 7) / 8 > INT_MAX) return ROSKO_ERR_INVALID_ARG;
+    if (items < 0 || items > INT_MAX) return ROSKO_ERR_UNSUPPORTED;   // 31-bit item index
     if (items == 0) return ROSKO_OK;
     e->one<<<(unsigned)((items + 7) / 8), 256, e->smem, st>>>(T);
   } else {
     DirectTable<64> T;
     std::memset(static_cast<void*>(&T), 0, sizeof(T));
     const int64_t items = fill(T);
-    if (items < 0 || (items + 7) / 8 > INT_MAX) return ROSKO_ERR_INVALID_ARG;
+    if (items < 0 || items > INT_MAX) return ROSKO_ERR_UNSUPPORTED;   // 31-bit item index
     if (items == 0) return ROSKO_OK;
     e->many<<<(unsigned)((items + 7) / 8), 256, e->smem, st>>>(T);
   }

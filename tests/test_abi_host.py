@@ -77,9 +77,15 @@ def test_analytic_schedule_fits_gb300(M, K, N, s, dt):
     assert t["m_r"] in (8, 16, 32)
     V = t["n_r"] // 32
     assert t["n_r"] % 32 == 0
-    # register level: m_r x V accumulators per lane within the 128-register budget
-    acc_words = t["m_r"] * V * (2 if dt == 3 else 1)
+    # register level: m_r x V accumulators per lane within the 128-register
+    # budget for the slab traversals; row-direct (order 4) holds one row of V
+    # columns per warp, at most two 16-byte chunks per lane
+    rows = 1 if t["order"] == 4 else t["m_r"]
+    acc_words = rows * V * (2 if dt == 3 else 1)
     assert acc_words <= 128
+    if t["order"] == 4:
+        esz = {0: 4, 1: 2, 2: 1, 3: 4}[dt]
+        assert V * esz <= 32
     # shared-memory level: the 4-stage B ring leaves room for two CTAs per SM
     esz = {0: 4, 1: 2, 2: 1, 3: 4}[dt]
     assert 1024 + 4 * t["k_c"] * t["n_r"] * esz <= 114 * 1024

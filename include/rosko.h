@@ -76,11 +76,11 @@ typedef enum {
  *   k_c   rows of B staged in shared memory per pipeline slab.
  *   m_c   C rows per CTA = warps per CTA x m_r.
  *   split_k  number of K ranges reduced into C with atomics (>= 1).
- *   dense_split_pm  BF16 only: 128-row tiles of A whose density in per mille
- *         (nonzeros per 1000 entries) is >= this value run on the tensor-core
- *         dense-panel path, the others on the sparse path; >= 1001 = never.
- *         At pack time the same field is the minimum density for which a
- *         dense copy is kept.
+ *   dense_split_pm  BF16, and INT8 with an INT32 result: 128-row tiles of A
+ *         whose density in per mille (nonzeros per 1000 entries) is >= this
+ *         value run on the tensor-core dense-panel path, the others on the
+ *         sparse path; >= 1001 = never.  At pack time the same field is the
+ *         minimum density for which a dense copy is kept.
  *   dense_n_r      C columns per tensor-core CTA tile (128 or 256).
  *   dense_split_k  CTAs over which the stream-K tensor-core path divides its
  *         (tile, K slab) work (default: one per SM); a tile whose K range
@@ -130,9 +130,10 @@ const char* rosko_status_string(rosko_status s);
  *           F64  from F32 (exact widening; FP64 check mode).
  * Limits: at most 65535 panels (M <= 65535 * m_r) and M * K < 2^31.
  * row_scale_dev  I8-from-I8 only: M FP32 row scales (device), else NULL.
- * tile    only tile->m_r and, for BF16, tile->dense_split_pm (minimum tile
- *         density, per mille, for keeping a dense copy; <= 0: 1 per mille)
- *         are read.
+ * tile    only tile->m_r and, for BF16 and INT8, tile->dense_split_pm
+ *         (minimum tile density, per mille, for keeping a dense BF16 copy of
+ *         the tile - the values, or the INT8 codes; <= 0: 1 per mille for
+ *         BF16, 10 for INT8) are read.
  *         m_r <= 0: 16.
  * out     receives the new handle (set to NULL on error).
  * Zero test: IEEE a != 0, so -0.0 is dropped and NaN/Inf are kept.
@@ -177,6 +178,13 @@ rosko_status rosko_pack_transposed(const void* A_dev, rosko_dtype a_dtype, int64
  * differ run to run in the last bits.  N may be 0 (no-op).
  * Dense-panel tiles (BF16) multiply their explicit zeros too, so there a
  * non-finite B value meets 0 * Inf = NaN, while skipped rows never see it.
+ * INT8 packs with an INT32 result run their dense-enough tiles on the same
+ * tensor-core path, exactly: the codes are integers exact in BF16, every K
+ * chunk of at most 1024 sums below 2^24 in magnitude (exact in the FP32
+ * accumulator) and is added into C as INT32, so the result is bit-identical
+ * to the integer sum; the call converts B to BF16 in stream-ordered scratch
+ * (K x N x 2 bytes, cudaMallocAsync / cudaFreeAsync on `stream`).  The FP32
+ * (dequantised) INT8 result stays on the CUDA-core path.
  * The row-direct traversal numbers its work items (row pieces x column
  * strips of n_r columns) with 31 bits; beyond that it returns
  * ROSKO_ERR_UNSUPPORTED.

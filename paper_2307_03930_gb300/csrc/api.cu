@@ -195,6 +195,12 @@ void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, i
 // (the autotuner and the selector refine it per shape).
 constexpr int kDenseSplitPm = 15;
 constexpr int kDenseCopyPm = 1;
+// INT8 codes through the BF16 tensor pipe (exact, K chunks of 1024 added into
+// INT32 C): against ~15 TOPS of 2*nnz*N for the INT8 row-direct kernel
+// (c3 shapes) the break-even tile density is again near 1.5%; dense copies of
+// INT8 packs are kept from 1% (the copies are BF16: twice the INT8 bytes).
+constexpr int kDenseSplitPmI8 = 15;
+constexpr int kDenseCopyPmI8 = 10;
 
 // ---------------------------------------------------------------------------
 // Analytic schedule: Sec. 4.2 re-derived for one GB300.
@@ -250,17 +256,22 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
   t->k_c = KC;
   t->m_c = W * m_r;
   t->split_k = (int32_t)split;
-  t->dense_split_pm = (dt == ROSKO_BF16) ? kDenseSplitPm : 1001;
+  t->dense_split_pm =
+      (dt == ROSKO_BF16) ? kDenseSplitPm : (dt == ROSKO_I8 ? kDenseSplitPmI8 : 1001);
   if (dt == ROSKO_BF16 && order == 4) {
     // Small or very sparse layers: the tensor-core launch has a fixed cost
-    // (~6 us: set-up, the first cold loads, the epilogue).  Model both paths
-    // on the uniform-density assumption (every tile on one side of the
-    // threshold) and keep the layer sparse when row-direct is predicted
-    // faster.  Dense: work at ~0.8 PFLOP/s.  Row-direct (fitted to the
-    // 512 x 4608 x 3136 sweep from 90% to 99.8%): ~6 us plus the nnz * N
-    // BF16 values it moves from L2 at ~12 TB/s.
-    const double t_dense = 6.0 + 2.0 * (double)M * (double)K * (double)N / 0.8e15 * 1e6;
-    const double t_direct = 6.0 + (double)nnz * (double)N * 2.0 / 12e12 * 1e6;
+    // (set-up, the first cold loads, the epilogue) that row-direct does not.
+    // Model both paths on the uniform-density assumption (every tile on one
+    // side of the threshold) and keep the layer sparse when row-direct is
+    // predicted faster.  Both models are least-squares fits (relative error)
+    // to the measured sweep of 2,000 random layers (M, K in [64, 4096],
+    // N in [196, 12544], 70-99% sparse, every schedule timed): dense
+    // ~11 us + 2 M K N at ~0.56 PFLOP/s, row-direct ~5 us + the nnz * N
+    // BF16 values it moves at ~10 TB/s.  (Picking the faster path by these
+    // models costs 11% over the better of the two, against 47% for a model
+    // fitted to the single 512 x 4608 x 3136 layer.)
+    const double t_dense = 11.0 + 2.0 * (double)M * (double)K * (double)N / 0.56e15 * 1e6;
+    const double t_direct = 5.0 + (double)nnz * (double)N * 2.0 / 10e12 * 1e6;
     if (t_direct < t_dense) t->dense_split_pm = 1001;
   }
   int TN = 256, ds = 1;
@@ -322,8 +333,9 @@ rosko_status rosko_pack(const void* A_dev, rosko_dtype a_dtype, int64_t M, int64
   }
   const int64_t P = (M + m_r - 1) / m_r;
   if (P > 65535) return ROSKO_ERR_INVALID_ARG;
-  const int32_t dense_min = (tile && tile->dense_split_pm > 0) ? tile->dense_split_pm
-                                                                 : kDenseCopyPm;
+  const int32_t dense_min = (tile && tile->dense_split_pm > 0)
+                                ? tile->dense_split_pm
+                                : (packed_dtype == ROSKO_I8 ? kDenseCopyPmI8 : kDenseCopyPm);
   rosko_packed_s* h = nullptr;
   rosko_status s = pack_impl(A_dev, a_dtype, M, K, lda, packed_dtype, row_scale_dev, m_r,
                              dense_min, static_cast<cudaStream_t>(stream), &h);
@@ -481,7 +493,9 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
   }
   // ---- dense-panel split: a prefix of the density-sorted dense copies ----
   int64_t n_dense = 0, dense_panels = 0;
-  if (p == ROSKO_BF16 && A->n_copy > 0 && t.dense_split_pm <= 1000) {
+  // tensor-core tiles: BF16, or INT8 codes with an INT32 result (exact)
+  const bool tc_ok = p == ROSKO_BF16 || (p == ROSKO_I8 && c_dtype == ROSKO_I32);
+  if (tc_ok && A->n_copy > 0 && t.dense_split_pm <= 1000) {
     while (n_dense < A->n_copy &&
            A->tile_density[(size_t)n_dense] * 1000.0 >= (double)t.dense_split_pm) {
       dense_panels += A->tile_panels[(size_t)A->tile_order[(size_t)n_dense]];
@@ -569,11 +583,12 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
     if (!direct_segments(A, A->panel_order_dev, n_sparse, which, &ns, &direct_cut))
       return ROSKO_ERR_UNSUPPORTED;
   }
+  // (INT8 tensor-core tiles add every K chunk into C)
   const bool zero_c =
       !accumulate && ((n_sparse > 0 && (L.split > 1 || direct_cut)) ||
                       (!skip_dense && n_dense > 0 &&
-                       dense_needs_zero(n_dense, N, A->K, t.dense_n_r, t.dense_split_k,
-                                        t.dense_m_c / 128)));
+                       (p == ROSKO_I8 || dense_needs_zero(n_dense, N, A->K, t.dense_n_r,
+                                                          t.dense_split_k, t.dense_m_c / 128))));
   if (flags & kRunPlanOnly) {
     // report the split and the resolved schedule, launch nothing
     rosko_plan* out = g_plan_out;
@@ -594,10 +609,15 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
           cudaSuccess)
     return ROSKO_ERR_CUDA;
   if (n_dense > 0 && !skip_dense) {
-    rosko_status s = dense_spmm_launch(A->dense_A, A->n_copy * 128, A->Kpad, A->tile_order_dev,
-                                       n_dense, A->K, B_dev, N, ldb, static_cast<float*>(C_dev),
-                                       ldc, A->M, accumulate, t.dense_n_r, t.dense_split_k,
-                                       t.dense_m_c / 128, zero_c, st);
+    rosko_status s =
+        p == ROSKO_I8
+            ? dense_spmm_i8_launch(A, n_dense, static_cast<const int8_t*>(B_dev), N, ldb,
+                                   static_cast<int32_t*>(C_dev), ldc, t.dense_n_r,
+                                   t.dense_split_k, t.dense_m_c / 128, st)
+            : dense_spmm_launch(A->dense_A, A->n_copy * 128, A->Kpad, A->tile_order_dev, n_dense,
+                                A->K, B_dev, N, ldb, static_cast<float*>(C_dev), ldc, A->M,
+                                accumulate, t.dense_n_r, t.dense_split_k, t.dense_m_c / 128,
+                                zero_c, st);
     if (s != ROSKO_OK) return s;
   }
   if (L.order == 3) {
@@ -659,6 +679,8 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
       const rosko_tile& u = tiles[i];
       if (u.dense_split_pm > 0) t.dense_split_pm = u.dense_split_pm;
     }
+    // the batch's tensor-core launches are BF16 only: other packs run sparse
+    if (A[i]->dt != ROSKO_BF16) t.dense_split_pm = 1001;
     int64_t nd = 0, dp = 0;
     dense_prefix(A[i], t.dense_split_pm, &nd, &dp);
     if (nd > 0) {

@@ -40,6 +40,15 @@ constexpr int kNumFeatures = 16;
 // into C atomically, so that power-law rows do not serialise on one warp
 // while rows of an even matrix stay whole.
 constexpr int kSegRecords = 64;
+// One work segment: {row, first record, end record, cut} and, inline, the
+// first 48 bytes of the piece's records (12 BF16 / INT8 records, 6 FP32,
+// 3 FP64), so that a warp whose piece fits starts its B loads one dependent
+// load earlier.  64 bytes: two sectors, one coalesced load of 16 lanes.
+struct SegEntry {
+  int4 head;
+  uint32_t rec[12];
+};
+static_assert(sizeof(SegEntry) == 64, "a segment entry is 64 bytes");
 inline int64_t seg_records_for(int64_t nnz, int64_t M) {
   const int64_t twice_mean = M > 0 ? (2 * nnz + M - 1) / M : 0;
   return std::max<int64_t>(kSegRecords, (twice_mean + 31) / 32 * 32);
@@ -72,15 +81,20 @@ struct rosko_packed_s {
   // 0 cuts every row into pieces of at most kSegRecords nonzeros (many
   // warps for few or long rows), list 1 only rows longer than
   // seg_records_for (twice the mean; few atomics for even matrices).  Per
-  // list: one int4 {row, first record, end record, cut} per segment (the
-  // record range of the piece in the row stream, sentinel excluded; cut = 1
-  // when the row has several pieces) in row order (nat) and in panel_order
-  // order (ord, BF16 packs with dense copies); prefix[i] / split[i] count the
-  // segments / the panels with a cut row among the first i panels of
-  // panel_order (or of the natural order without one).
+  // list: one SegEntry per segment (head = the record range of the piece in
+  // the row stream, sentinel excluded, and cut = 1 when the row has several
+  // pieces; then the piece's first records) in row order (nat) and in
+  // panel_order order (ord, packs with dense copies); prefix[i] / split[i]
+  // count the segments / the panels with a cut row among the first i panels
+  // of panel_order (or of the natural order without one).
+  // lpt: every segment of the list, longest piece first (ties in row
+  // order) - the order of a launch that runs all panels sparse, so that the
+  // longest pieces start first and the 8 items of a block have similar
+  // lengths (an inspector-executor ordering of the work, fixed at pack time).
   struct SegList {
-    int4* nat = nullptr;
-    int4* ord = nullptr;
+    SegEntry* nat = nullptr;
+    SegEntry* ord = nullptr;
+    SegEntry* lpt = nullptr;
     std::vector<int64_t> prefix;
     std::vector<int32_t> split;
     int32_t records = kSegRecords;
@@ -182,7 +196,7 @@ struct DirectJob {
 // is of another kind.  *cut: some listed row is cut into several pieces
 // (their sums are added into C, which must then be zeroed unless the call
 // accumulates).
-const int4* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
+const SegEntry* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
                             int which, int64_t* n_segs, bool* cut);
 // The list a launch over these panels with width N and V columns per lane
 // uses (0 fine, 1 coarse); decided the same way for zero-fill and launch.
@@ -203,7 +217,16 @@ struct DenseJob {
   float* C;
   int64_t ldc, M;
   int accumulate;
+  int kchunk = 0;    // K slabs per exact-integer chunk (INT8 codes), 0: none
+  int out_i32 = 0;   // C is INT32 (INT8 codes through the BF16 pipe)
 };
+// INT8 x INT8 -> INT32 through the BF16 tensor pipe: B is converted to BF16
+// (exact) in stream-ordered scratch, the handle's dense copies hold the INT8
+// codes as BF16, and every K chunk of <= 1024 (exact in FP32) is converted
+// and added into C, which the caller has zeroed unless it accumulates.
+rosko_status dense_spmm_i8_launch(const rosko_packed_s* h, int64_t n_tiles, const int8_t* B,
+                                  int64_t N, int64_t ldb, int32_t* C, int64_t ldc, int TN,
+                                  int ctas, int MH, cudaStream_t st);
 // One persistent stream-K launch over all jobs' dense tiles (count <= 64);
 // C of jobs whose tiles the split cuts must be zeroed by the caller unless
 // they accumulate (dense_batch_needs_zero).

@@ -228,8 +228,9 @@ __global__ void scan_down_kernel(ScanSet s) {
 // Dense BF16 copies of 128-row tiles for the tensor-core dense-panel path:
 // row block c holds rows tile_order[c]*128 .. +127 of A (zero past M and past
 // K; row stride Kpad), converted exactly as the packer converts them.
-__device__ __forceinline__ __nv_bfloat16 to_bf16(float a) { return __float2bfloat16_rn(a); }
 __device__ __forceinline__ __nv_bfloat16 to_bf16(__nv_bfloat16 a) { return a; }
+// INT8 codes are integers of magnitude <= 127: exact in BF16
+__device__ __forceinline__ __nv_bfloat16 to_bf16(int8_t a) { return __float2bfloat16_rn((float)a); }
 
 // Row-slot stream records (value + column k) and the per-row sentinel.
 __device__ __forceinline__ void put_row_rec(void* rnz, int64_t e, float v, int k) {
@@ -468,16 +469,22 @@ __device__ void tile_union(const PackGeom& g, int64_t b, const WriteArgs& w) {
   if (w.flag[i + 1].x != w.flag[i].x) w.gu_k[w.flag[i].x] = (int32_t)k;
 }
 
-template <class S>
-__device__ void densify(const S* __restrict__ A, const PackGeom& g, int64_t b,
-                        const WriteArgs& w) {
+// The dense copy holds each entry converted exactly as the packer converts
+// it (BF16 packs: the BF16 value; INT8 packs: the INT8 code, exact in BF16).
+template <class S, class D>
+__device__ void densify(const S* __restrict__ A, const PackGeom& g,
+                        const float* __restrict__ scale, int64_t b, const WriteArgs& w) {
   const int64_t k = (b % w.gxd) * kPackThreads + threadIdx.x;
   if (k >= w.Kpad) return;
   for (int64_t rr = b / w.gxd; rr < w.dense_rows; rr += w.ry) {
     const int64_t row = (int64_t)w.tile_order[rr / kDenseTileRows] * kDenseTileRows +
                         rr % kDenseTileRows;
     __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-    if (row < g.M && k < g.K) v = to_bf16(A[row * g.lda + k]);
+    if (row < g.M && k < g.K) {
+      D q;
+      Conv<S, D>::get(A[row * g.lda + k], scale ? scale[row] : 1.0f, q);
+      v = to_bf16(q);
+    }
     w.dense_A[rr * w.Kpad + k] = v;
   }
 }
@@ -524,9 +531,9 @@ __global__ void __launch_bounds__(kPackThreads)
     return;
   }
   b -= w.b_union;
-  if constexpr (std::is_same<D, __nv_bfloat16>::value) {
+  if constexpr (std::is_same<D, __nv_bfloat16>::value || std::is_same<D, int8_t>::value) {
     if (b < w.b_dense) {
-      densify<S>(A, g, b, w);
+      densify<S, D>(A, g, scale, b, w);
       return;
     }
   }
@@ -625,7 +632,8 @@ void plan_dense_tiles(rosko_packed_s* h, int32_t dense_min_pm) {
 // at both granularities: {row, first record, end record, cut} in row order
 // (nat) and, with a panel order, in that order (ord).
 void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32_t>* panel_order,
-                   std::vector<int4> nat[2], std::vector<int4> ord[2]) {
+                   std::vector<SegEntry> nat[2], std::vector<SegEntry> ord[2],
+                   std::vector<SegEntry> lpt[2]) {
   const int64_t M = h->M, P = h->P;
   const int64_t lens[2] = {kSegRecords, seg_records_for(h->nnz, M)};
   for (int g = 0; g < 2; ++g) {
@@ -644,8 +652,11 @@ void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32
         const int64_t row_end = (int64_t)rp[r + 1] - 1;
         for (int64_t k = 0; k < ns; ++k) {
           const int64_t e0 = (int64_t)rp[r] + k * seg;
-          nat[g].push_back(make_int4((int)r, (int)e0, (int)std::min<int64_t>(e0 + seg, row_end),
-                                     ns > 1 ? 1 : 0));
+          SegEntry se;
+          std::memset(&se, 0, sizeof(se));
+          se.head = make_int4((int)r, (int)e0, (int)std::min<int64_t>(e0 + seg, row_end),
+                              ns > 1 ? 1 : 0);
+          nat[g].push_back(se);   // inline records: written on the device
         }
       }
     }
@@ -660,7 +671,33 @@ void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32
       L.prefix[(size_t)i + 1] = L.prefix[(size_t)i] + (panel_seg[(size_t)p + 1] - panel_seg[(size_t)p]);
       L.split[(size_t)i + 1] = L.split[(size_t)i] + panel_split[(size_t)p];
     }
+    lpt[g] = nat[g];
+    std::stable_sort(lpt[g].begin(), lpt[g].end(), [](const SegEntry& a, const SegEntry& b) {
+      return a.head.z - a.head.y > b.head.z - b.head.y;
+    });
   }
+}
+
+// Inline records of the work segments: the first 48 bytes of each piece's
+// records in the row stream (written by the phase-2 launch) copied into its
+// entry; one thread per (segment, 4-byte word), over up to four lists.
+struct InlineLists {
+  SegEntry* list[6];
+  int64_t n[6];
+  int64_t first[7];   // first thread of each list
+};
+__global__ void seg_inline_kernel(InlineLists L, const uint32_t* __restrict__ rnz, int rec_words) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int l = 0;
+  while (l < 5 && t >= L.first[l + 1]) ++l;
+  if (t >= L.first[6]) return;
+  const int64_t local = t - L.first[l];
+  const int64_t s = local / 12;
+  const int w = (int)(local - s * 12);
+  SegEntry& e = L.list[l][s];
+  const int64_t words = (int64_t)(e.head.z - e.head.y) * rec_words;
+  if (w < words && w / rec_words < 12 / rec_words)
+    e.rec[w] = rnz[(int64_t)e.head.y * rec_words + w];
 }
 
 // Bump allocator over byte offsets, each region 256-byte aligned.
@@ -689,8 +726,8 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
   const int64_t T = (M + kDenseTileRows - 1) / kDenseTileRows;
   const bool rows = M > 0 && K < kRowSlotMaxK;
   const bool gather = rows && h->m_r == 16 && K > 0;
-  const bool dense =
-      std::is_same<D, __nv_bfloat16>::value && dense_min_pm <= 1000 && M > 0 && K > 0;
+  const bool dense = (std::is_same<D, __nv_bfloat16>::value || std::is_same<D, int8_t>::value) &&
+                     dense_min_pm <= 1000 && M > 0 && K > 0;
   const int64_t nf = gather ? T * K : 0;
   auto blocks_for = [](int64_t x) { return (x + kScanTile - 1) / kScanTile + 1; };
 
@@ -802,8 +839,8 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
                                               (o_rp - o_sum64))
            : nullptr;
   if (dense) plan_dense_tiles(h, dense_min_pm);
-  std::vector<int4> nat[2], ord[2];
-  if (rows) plan_segments(h, rp, dense ? &h->panel_order_host : nullptr, nat, ord);
+  std::vector<SegEntry> nat[2], ord[2], lpt[2];
+  if (rows) plan_segments(h, rp, dense ? &h->panel_order_host : nullptr, nat, ord, lpt);
 
   const size_t rsz = rec_size(h->dt);
   const int64_t nnz = h->nnz, n_cols = h->n_cols;
@@ -811,10 +848,11 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
   // staged from the host in one copy
   const size_t o_to = L.take(dense ? (size_t)T * 4 : 0);
   const size_t o_po = L.take(dense ? (size_t)P * 4 : 0);
-  size_t o_seg[4];
+  size_t o_seg[6];
   for (int g = 0; g < 2; ++g) {
-    o_seg[2 * g] = L.take(nat[g].size() * sizeof(int4));
-    o_seg[2 * g + 1] = L.take(ord[g].size() * sizeof(int4));
+    o_seg[3 * g] = L.take(nat[g].size() * sizeof(SegEntry));
+    o_seg[3 * g + 1] = L.take(ord[g].size() * sizeof(SegEntry));
+    o_seg[3 * g + 2] = L.take(lpt[g].size() * sizeof(SegEntry));
   }
   const size_t staged = L.top;
   // written on the device
@@ -844,8 +882,9 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
     h->rowptr = reinterpret_cast<int32_t*>(b + o_rowptr);
     h->rnz = b + o_rnz;
     for (int g = 0; g < 2; ++g) {
-      h->segs[g].nat = reinterpret_cast<int4*>(b + o_seg[2 * g]);
-      h->segs[g].ord = dense ? reinterpret_cast<int4*>(b + o_seg[2 * g + 1]) : nullptr;
+      h->segs[g].nat = reinterpret_cast<SegEntry*>(b + o_seg[3 * g]);
+      h->segs[g].ord = dense ? reinterpret_cast<SegEntry*>(b + o_seg[3 * g + 1]) : nullptr;
+      h->segs[g].lpt = reinterpret_cast<SegEntry*>(b + o_seg[3 * g + 2]);
     }
   }
   if (gather) {
@@ -866,9 +905,11 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
     }
     for (int g = 0; g < 2; ++g) {
       if (!nat[g].empty())
-        std::memcpy(stage.data() + o_seg[2 * g], nat[g].data(), nat[g].size() * sizeof(int4));
+        std::memcpy(stage.data() + o_seg[3 * g], nat[g].data(), nat[g].size() * sizeof(SegEntry));
       if (!ord[g].empty())
-        std::memcpy(stage.data() + o_seg[2 * g + 1], ord[g].data(), ord[g].size() * sizeof(int4));
+        std::memcpy(stage.data() + o_seg[3 * g + 1], ord[g].data(), ord[g].size() * sizeof(SegEntry));
+      if (!lpt[g].empty())
+        std::memcpy(stage.data() + o_seg[3 * g + 2], lpt[g].data(), lpt[g].size() * sizeof(SegEntry));
     }
     // a pageable source is staged before the call returns
     if (cudaMemcpyAsync(b, stage.data(), staged, cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -925,6 +966,33 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
       <<<(unsigned)(w.b_scatter + w.b_row + w.b_union + w.b_dense + 1), kPackThreads, 0, st>>>(
           A, geo, scale, w);
   count_launches(1);
+  if (rows) {
+    // the segments' inline records, once the row stream is written
+    InlineLists il;
+    std::memset(&il, 0, sizeof(il));
+    int nl = 0;
+    for (int g = 0; g < 2; ++g) {
+      if (h->segs[g].nat && !nat[g].empty()) {
+        il.list[nl] = h->segs[g].nat;
+        il.n[nl++] = (int64_t)nat[g].size();
+      }
+      if (h->segs[g].ord && !ord[g].empty()) {
+        il.list[nl] = h->segs[g].ord;
+        il.n[nl++] = (int64_t)ord[g].size();
+      }
+      if (h->segs[g].lpt && !lpt[g].empty()) {
+        il.list[nl] = h->segs[g].lpt;
+        il.n[nl++] = (int64_t)lpt[g].size();
+      }
+    }
+    il.first[0] = 0;
+    for (int l = 0; l < 6; ++l) il.first[l + 1] = il.first[l] + (l < nl ? il.n[l] * 12 : 0);
+    if (il.first[6] > 0) {
+      seg_inline_kernel<<<(unsigned)((il.first[6] + 255) / 256), 256, 0, st>>>(
+          il, static_cast<const uint32_t*>(h->rnz), (int)(rsz / 4));
+      count_launches(1);
+    }
+  }
   // the scratch is released on return: wait for the writes that read it
   if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return ROSKO_ERR_CUDA;

@@ -22,7 +22,7 @@ namespace {
 
 constexpr uint64_t kImageMagic = 0x31504b4f4b534f52ull;  // "ROSKOKP1"
 constexpr uint32_t kImageVersion = 1;
-constexpr int kNumPtrs = 18;
+constexpr int kNumPtrs = 20;
 
 struct Header {
   uint64_t magic;
@@ -65,6 +65,8 @@ void** ptr_slots(rosko_packed_s* h, void** slots[kNumPtrs]) {
   slots[i++] = reinterpret_cast<void**>(&h->segs[0].ord);
   slots[i++] = reinterpret_cast<void**>(&h->segs[1].nat);
   slots[i++] = reinterpret_cast<void**>(&h->segs[1].ord);
+  slots[i++] = reinterpret_cast<void**>(&h->segs[0].lpt);
+  slots[i++] = reinterpret_cast<void**>(&h->segs[1].lpt);
   return slots[0];
 }
 

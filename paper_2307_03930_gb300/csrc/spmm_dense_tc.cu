@@ -78,6 +78,11 @@ struct DenseTable {
   int64_t units;
   int stages;
   int aligned;   // CTA ranges start and end on tile boundaries (no tile is cut)
+  // INT8 codes through the BF16 pipe: accumulator segments end every
+  // `kchunk` K slabs (0: only at tile ends), so that every FP32 partial sum
+  // stays an exact integer, and C is INT32 (partials converted and added)
+  int kchunk;
+  int out_i32;
   int* status;
 };
 
@@ -266,8 +271,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t bph = 1;         // its acc_empty parity (flips each reuse)
       for (int64_t u = u0; u < u1 && ok; ++u) {
         const int slab = c.slab;
-        const bool first = (u == u0) || slab == 0;
-        const bool last = (u + 1 == u1) || slab + 1 == c.slabs;
+        const int kc = T.kchunk;
+        const bool first = (u == u0) || slab == 0 || (kc && slab % kc == 0);
+        const bool last = (u + 1 == u1) || slab + 1 == c.slabs || (kc && (slab + 1) % kc == 0);
         if (first) {
           ++seg;
           if (++bsel == NBUF) {
@@ -330,7 +336,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t u = u0; u < u1;) {
       const DenseProb& P = T.p[c.q];
       const int q = c.q;
-      int64_t ue = u + (c.slabs - c.slab);
+      // the segment ends at the tile's end, the K chunk's end or the range's
+      const int seg_end = T.kchunk ? min(c.slabs, (c.slab / T.kchunk + 1) * T.kchunk) : c.slabs;
+      int64_t ue = u + (seg_end - c.slab);
       if (ue > u1) ue = u1;
       const bool whole = (c.slab == 0) && (ue - u == c.slabs);
       const int mt = c.mt, nt = c.nt;
@@ -347,7 +355,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int copy = mt * MH + hh;
         if (copy >= P.n_copy) break;   // warp-uniform
         const int64_t row0 = (int64_t)__ldg(&P.tile_order[copy]) * kTM + quarter * 32;
-        const int64_t row = row0 + lane;
 #pragma unroll 1
         for (int cc = part * (TN / 32 / kParts); cc < (part + 1) * (TN / 32 / kParts); ++cc) {
           uint32_t r[32];
@@ -357,6 +364,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc::tmem_ld_wait();
           const int64_t col0 = n0 + cc * 32;
           if (!ok || row0 >= P.M || col0 >= P.N) continue;   // warp-uniform
+          if (T.out_i32) {
+            // an exact integer in FP32 (|partial| < 2^24): convert to INT32
+#pragma unroll
+            for (int j = 0; j < 32; ++j) r[j] = (uint32_t)__float2int_rn(__uint_as_float(r[j]));
+          }
           if (P.tma_c) {
             // staging tile (chunk & 1) is free once the copy issued two
             // chunks ago has read it
@@ -399,8 +411,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int rr = 0; rr < rows; ++rr) {
               const float v = tr[rr * 32 + ((lane + rr) & 31)];
               float* dst = P.C + (row0 + rr) * P.ldc + col;
-              if (add) atomicAdd(dst, v);   // a cut tile, or C += A.B
-              else *dst = v;
+              if (T.out_i32) {
+                int* di = reinterpret_cast<int*>(dst);
+                const int iv = (int)__float_as_uint(v);   // already converted
+                if (add) atomicAdd(di, iv);
+                else *di = iv;
+              } else if (add) {
+                atomicAdd(dst, v);   // a cut tile, or C += A.B
+              } else {
+                *dst = v;
+              }
             }
           }
         }
@@ -409,8 +429,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
+      const int adv = (int)(ue - u);
       u = ue;
-      cursor_next_tile<NP, MH>(T, c);
+      if (c.slab + adv >= c.slabs) cursor_next_tile<NP, MH>(T, c);
+      else c.slab += adv;   // the next K chunk of the same tile
     }
     // the staging tiles must not be released (CTA exit) while TMA reads
     // them, and C must be complete when the kernel ends
@@ -459,7 +481,8 @@ rosko_status encode_dense_maps(const DenseJob& j, int MH, CUtensorMap* mA, CUten
     const cuuint64_t strides[1] = {(cuuint64_t)j.ldc * 4};
     const cuuint32_t box[2] = {32, 32};
     const cuuint32_t es[2] = {1, 1};
-    if (encode_tiled(mC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, j.C, dims, strides, box, es,
+    if (encode_tiled(mC, j.out_i32 ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                     2, j.C, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
@@ -557,6 +580,8 @@ rosko_status run_jobs(const DenseJob* jobs, int count, int ctas, cudaStream_t st
   for (int i = 0; i < n; ++i) tiles += (int64_t)((T.p[i].n_copy + MH - 1) / MH) * T.p[i].n_ntiles;
   const int64_t grid = grid_for(units, tiles, ctas);
   T.aligned = use_aligned(tiles, grid) ? 1 : 0;
+  T.kchunk = jobs[0].kchunk;
+  T.out_i32 = jobs[0].out_i32;
   T.stages = dense_stages<TN, MH>();
   T.status = device_status_word();
   if (!T.status) return ROSKO_ERR_CUDA;
@@ -634,6 +659,72 @@ rosko_status dense_batch_launch(const DenseJob* jobs, int count, int TN, int cta
   if (count == 1) return dispatch_jobs<1>(jobs, 1, TN, MH, ctas, st);
   if (count <= 64) return dispatch_jobs<64>(jobs, count, TN, MH, ctas, st);
   return ROSKO_ERR_INVALID_ARG;
+}
+
+namespace {
+// INT8 -> BF16 (exact: |code| <= 127), K rows of N, into rows of ldo.
+__global__ void i8_to_bf16_kernel(const int8_t* __restrict__ B, int64_t K, int64_t N, int64_t ldb,
+                                  __nv_bfloat16* __restrict__ out, int64_t ldo) {
+  const int64_t cols = (ldo + 3) / 4;   // four values per thread
+  const int64_t n = K * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / cols, c0 = (i - k * cols) * 4;
+    __nv_bfloat16 v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t c = c0 + j;
+      v[j] = __float2bfloat16_rn(c < N ? (float)B[k * ldb + c] : 0.0f);
+      if (c < ldo) out[k * ldo + c] = v[j];
+    }
+  }
+}
+}  // namespace
+
+// K slabs of 64 per exact chunk: 16 slabs = 1024 products of magnitude
+// <= 127^2, so a partial sum stays below 1024 * 16129 < 2^24 and is exact in
+// the FP32 accumulator.
+constexpr int kI8ChunkSlabs = 16;
+
+rosko_status dense_spmm_i8_launch(const rosko_packed_s* h, int64_t n_tiles, const int8_t* B,
+                                  int64_t N, int64_t ldb, int32_t* C, int64_t ldc, int TN,
+                                  int ctas, int MH, cudaStream_t st) {
+  if (n_tiles <= 0 || N <= 0) return ROSKO_OK;
+  if (TN != 128 && TN != 256) return ROSKO_ERR_INVALID_ARG;
+  if (ctas <= 0) ctas = num_sms();
+  const int64_t K = h->K;
+  const int64_t ldo = (N + 7) / 8 * 8;   // 16-byte rows for the tensor map
+  void* scratch = nullptr;
+  // stream-ordered (and capturable): released after the launch that reads it
+  if (cudaMallocAsync(&scratch, (size_t)std::max<int64_t>(K * ldo, 1) * 2, st) != cudaSuccess)
+    return ROSKO_ERR_OOM;
+  const int64_t work = K * ((ldo + 3) / 4);
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096));
+  i8_to_bf16_kernel<<<blocks, 256, 0, st>>>(B, K, N, ldb, static_cast<__nv_bfloat16*>(scratch),
+                                            ldo);
+  count_launches(1);
+  rosko_status s = cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+  if (s == ROSKO_OK) {
+    DenseJob j;
+    j.dense_A = h->dense_A;
+    j.dense_rows = h->n_copy * kTM;
+    j.Kpad = h->Kpad;
+    j.tile_order_dev = h->tile_order_dev;
+    j.n_tiles = n_tiles;
+    j.K = K;
+    j.B = scratch;
+    j.N = N;
+    j.ldb = ldo;
+    j.C = reinterpret_cast<float*>(C);
+    j.ldc = ldc;
+    j.M = h->M;
+    j.accumulate = 1;   // every chunk adds into the zeroed (or accumulated) C
+    j.kchunk = kI8ChunkSlabs;
+    j.out_i32 = 1;
+    s = dense_batch_launch(&j, 1, TN, ctas, MH, st);
+  }
+  cudaFreeAsync(scratch, st);
+  return s;
 }
 
 rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t Kpad,

@@ -543,7 +543,7 @@ __device__ __forceinline__ void fma_bf16x2(float& c0, float& c1, uint32_t rec, u
 
 struct DirectProb {
   const void* rnz;            // row stream: per-row k-ascending records + sentinel
-  const int4* segs;           // work segments {row, e0, e_end, cut}
+  const SegEntry* segs;       // work segments: {row, e0, e_end, cut} + inline records
   const float* row_scale;     // INT8 dequantisation
   const float* col_scale;
   const void* B;
@@ -675,7 +675,23 @@ __global__ void __launch_bounds__(256, 3)
   const int local = it - (int)P.items0;
   const int si = local / P.strips;
   const int strip = local - si * P.strips;
-  const int4 seg = ld_keep(&P.segs[si], keep);
+  // the segment entry (64 bytes, one coalesced load of 16 lanes): its head
+  // and the piece's first records
+  const uint32_t wv =
+      lane < 16 ? ld_keep(reinterpret_cast<const uint32_t*>(&P.segs[si]) + lane, keep) : 0u;
+  const int4 seg = make_int4((int)__shfl_sync(0xffffffffu, wv, 0),
+                             (int)__shfl_sync(0xffffffffu, wv, 1),
+                             (int)__shfl_sync(0xffffffffu, wv, 2),
+                             (int)__shfl_sync(0xffffffffu, wv, 3));
+  constexpr int RW = (int)sizeof(WT) / 4;   // words per record
+  constexpr int NI = 12 / RW;               // records held inline
+  WT inl;
+  {
+    uint32_t iw[RW];
+#pragma unroll
+    for (int j = 0; j < RW; ++j) iw[j] = __shfl_sync(0xffffffffu, wv, 4 + (lane % NI) * RW + j);
+    memcpy(&inl, iw, sizeof(WT));
+  }
   const int64_t row = seg.x;
   const int e0 = seg.y, e_end = seg.z;
   const bool cut = seg.w != 0;
@@ -790,7 +806,8 @@ __global__ void __launch_bounds__(256, 3)
   // two halves of the ring
   // records stay in L2 across launches (evict last): e_end is the row's
   // sentinel or the next piece's first record, always inside the stream
-  WT mine = ld_keep(&rnz[lane < e_end - e0 ? e0 + lane : e_end], keep);
+  // a piece of at most NI records needs no record load at all
+  WT mine = e_end - e0 <= NI ? inl : ld_keep(&rnz[lane < e_end - e0 ? e0 + lane : e_end], keep);
   for (int base = e0; base < e_end; base += 32) {
     const int cnt = min(32, e_end - base);
     WT nmine = mine;
@@ -977,14 +994,18 @@ int sparse_default_V(rosko_dtype p_dt, int R, int order) {
 // handle's panel_order with n_panels its first entries); *n_segs receives
 // their count, *cut whether one of those rows is cut into several pieces.
 // NULL for a list of another kind.
-const int4* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
-                            int which, int64_t* n_segs, bool* cut) {
+const SegEntry* direct_segments(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels,
+                                int which, int64_t* n_segs, bool* cut) {
   if (cut) *cut = false;
   *n_segs = -1;
   const rosko_packed_s::SegList& L = h->segs[which & 1];
   if (!L.nat || n_panels < 0 || n_panels > h->P) return nullptr;
-  const int4* base;
-  if (!panel_list) {
+  const SegEntry* base;
+  if (n_panels == h->P && L.lpt && (!panel_list || panel_list == h->panel_order_dev)) {
+    // every panel runs sparse: any order of all segments covers them, and
+    // the longest-first order balances the launch
+    base = L.lpt;
+  } else if (!panel_list) {
     // all panels in order (the prefix sums' last entry is the total in
     // either order)
     if (n_panels != h->P) return nullptr;
@@ -1019,7 +1040,7 @@ static int64_t direct_prob(const DirectJob& j, int V, int64_t items0, DirectProb
   if (reinterpret_cast<uintptr_t>(j.B) % 16 != 0 || (j.ldb * (int64_t)bsz) % 16 != 0) return -1;
   int64_t n_segs = 0;
   const int which = direct_pick(h, j.panel_list, j.n_panels, j.N, V);
-  const int4* segs = direct_segments(h, j.panel_list, j.n_panels, which, &n_segs, nullptr);
+  const SegEntry* segs = direct_segments(h, j.panel_list, j.n_panels, which, &n_segs, nullptr);
   if (!segs) return -1;
   std::memset(P, 0, sizeof(*P));
   P->rnz = h->rnz;

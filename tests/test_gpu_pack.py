@@ -162,8 +162,9 @@ def test_pack_launch_count(a_dt, p_dt):
     # the independent passes of each phase share one launch: counting (panel
     # columns, rows, tile columns), the three launches of the fused scans,
     # the size summary, then writing (column records, row and gather streams,
-    # union lists, dense copies, terminating entries); INT8 adds its row
-    # scales (quantisation from FP32, or the all-ones default)
+    # union lists, dense copies, terminating entries), then the work
+    # segments' inline records; INT8 adds its row scales (quantisation from
+    # FP32, or the all-ones default)
     rosko = built()
     A = _matrix(300, 500, 0.9, seed=5)
     if a_dt == "bf16":
@@ -175,7 +176,7 @@ def test_pack_launch_count(a_dt, p_dt):
     torch.cuda.synchronize()
     l0 = rosko.rosko_kernel_launches()
     h = rosko.rosko_pack(At, CODES[p_dt])
-    assert rosko.rosko_kernel_launches() - l0 == 6 + (p_dt == "i8")
+    assert rosko.rosko_kernel_launches() - l0 == 7 + (p_dt == "i8")
     nnz = int((At != 0).sum())
     # quantisation from FP32 also drops the values whose code rounds to 0
     assert h.info()["nnz"] == nnz if a_dt == p_dt or p_dt != "i8" else h.info()["nnz"] <= nnz

@@ -195,6 +195,58 @@ def regret(times: np.ndarray, analytic: np.ndarray, choice: np.ndarray) -> dict:
             "n": int(times.shape[0])}
 
 
+# Candidate columns of the sweep: sparse configuration i, dense threshold j
+# (index i * 5 + j); the analytic rule's row-direct configurations are
+# i = 3 (512-column strips) and i = 11 (256), its thresholds j = 0 (never
+# dense) and j = 3 (15 per mille); j = 1 (1 per mille) is all-dense.
+N_DENSE_PM = 5
+
+
+def _relfit(x: np.ndarray, y: np.ndarray) -> tuple[float, float]:
+    """(a, b) minimising sum(((a + b x) / y - 1)^2): least squares in
+    relative error."""
+    A = np.stack([1.0 / y, x / y], 1)
+    sol, *_ = np.linalg.lstsq(A, np.ones_like(y), rcond=None)
+    return float(sol[0]), float(sol[1])
+
+
+def split_columns(features: np.ndarray, times: np.ndarray) -> dict:
+    """Shapes and the three timed paths the analytic rule chooses between,
+    per problem (times in microseconds)."""
+    f = np.asarray(features, dtype=np.float64)
+    M, K, N = (np.round(2.0 ** f[:, j]) for j in range(3))
+    nnz = np.round(f[:, 3] * M * K)
+    i_rd = np.where((f[:, 3] < 0.015) & (N >= 1024), 3, 11)
+    r = np.arange(len(f))
+    t = np.asarray(times, dtype=np.float64) * 1e3
+    return {"M": M, "K": K, "N": N, "nnz": nnz,
+            "direct": t[r, i_rd * N_DENSE_PM], "split": t[r, i_rd * N_DENSE_PM + 3],
+            "dense": t[r, i_rd * N_DENSE_PM + 1], "best": np.nanmin(t, axis=1)}
+
+
+def fit_split(features: np.ndarray, times: np.ndarray) -> dict:
+    """The analytic rule's two time models, fitted to a timed sweep: dense
+    t = a + 2 M K N / R_dense (all tiles on the tensor cores), row-direct
+    t = c + 2 nnz N / R_direct (BF16 bytes of B moved).  Returns the
+    constants (us, FLOP/s, B/s)."""
+    S = split_columns(features, times)
+    a, b = _relfit(2.0 * S["M"] * S["K"] * S["N"], S["dense"])
+    c, e = _relfit(2.0 * S["nnz"] * S["N"], S["direct"])
+    return {"dense_us": a, "dense_flops": 1e6 / b, "direct_us": c, "direct_bytes_s": 1e6 / e}
+
+
+def split_regret(features: np.ndarray, times: np.ndarray, m: dict) -> dict:
+    """Regret of choosing between row-direct and the 15-per-mille split by
+    the models m: against the best candidate and against the better of the
+    two paths."""
+    S = split_columns(features, times)
+    td = m["dense_us"] + 2.0 * S["M"] * S["K"] * S["N"] / m["dense_flops"] * 1e6
+    tr = m["direct_us"] + 2.0 * S["nnz"] * S["N"] / m["direct_bytes_s"] * 1e6
+    t = np.where(tr < td, S["direct"], S["split"])
+    return {"vs_best": float(np.mean(t / S["best"] - 1.0)),
+            "vs_better_of_two": float(np.mean(t / np.minimum(S["direct"], S["split"]) - 1.0))}
+
+
 def save(model: dict, path: str = WEIGHTS, extra: dict | None = None) -> None:
     np.savez(path, params=model["params"], mean=model["mean"], std=model["std"],
              lo=model["lo"], hi=model["hi"], info=json.dumps(extra or {}))
@@ -227,8 +279,17 @@ def main():
                     help="save the held-out split (features, times, analytic) as npz")
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--data-out", default=None, help="also save the sweep (npz)")
+    ap.add_argument("--fit-split", default=None, metavar="SWEEP_NPZ",
+                    help="fit the analytic rule's time models on a saved sweep's training "
+                         "split, print them with their held-out regret, and exit")
     a = ap.parse_args()
     t0 = time.time()
+    if a.fit_split:
+        d = np.load(a.fit_split)
+        m = fit_split(d["tr_f"], d["tr_t"])
+        print(json.dumps({"model": m, "train": split_regret(d["tr_f"], d["tr_t"], m),
+                          "heldout": split_regret(d["ho_f"], d["ho_t"], m)}), flush=True)
+        return
     if a.data_in:
         d = np.load(a.data_in)
         tr = {"features": d["tr_f"], "times": d["tr_t"], "analytic": d["tr_a"]}

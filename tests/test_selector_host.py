@@ -72,3 +72,38 @@ def test_sweep_problem_distributions():
         assert [p[5] for p in a] == list(range(300))
     # the two families draw from different streams
     assert sel.random_problems(4, 5, "layers") != sel.random_problems(4, 5, "conv")
+
+
+def _split_sweep(n, rng):
+    """Features and a 60-column time grid (ms) whose all-dense and
+    row-direct columns follow two known linear models exactly."""
+    M = rng.integers(64, 4096, n).astype(float)
+    K = rng.integers(64, 4096, n).astype(float)
+    N = rng.integers(196, 12544, n).astype(float)
+    d = rng.uniform(0.001, 0.3, n)
+    nnz = np.round(d * M * K)
+    f = np.zeros((n, 16))
+    f[:, 0], f[:, 1], f[:, 2] = np.log2(M), np.log2(K), np.log2(N)
+    f[:, 3] = nnz / (M * K)
+    t = np.full((n, 60), 1.0)                      # every other candidate slow
+    dense_us = 12.0 + 2 * M * K * N / 0.6e15 * 1e6
+    direct_us = 5.0 + 2 * nnz * N / 11e12 * 1e6
+    i_rd = np.where((f[:, 3] < 0.015) & (N >= 1024), 3, 11)
+    r = np.arange(n)
+    t[r, i_rd * 5 + 1] = dense_us * 1e-3
+    t[r, i_rd * 5] = direct_us * 1e-3
+    t[r, i_rd * 5 + 3] = dense_us * 1e-3
+    return f, t
+
+
+def test_fit_split_recovers_planted_models():
+    f, t = _split_sweep(400, np.random.default_rng(3))
+    m = sel.fit_split(f, t)
+    assert abs(m["dense_us"] - 12.0) < 1e-6 and abs(m["direct_us"] - 5.0) < 1e-6
+    assert abs(m["dense_flops"] / 0.6e15 - 1) < 1e-9 and abs(m["direct_bytes_s"] / 11e12 - 1) < 1e-9
+    # exact models choose the faster path every time: no regret
+    r = sel.split_regret(f, t, m)
+    assert r["vs_best"] == 0.0 and r["vs_better_of_two"] == 0.0
+    # swapping the two rates misroutes some layers: positive regret
+    bad = dict(m, dense_flops=m["direct_bytes_s"] * 50, direct_bytes_s=m["dense_flops"] / 50)
+    assert sel.split_regret(f, t, bad)["vs_better_of_two"] > 0.0

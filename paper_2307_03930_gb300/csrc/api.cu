@@ -162,11 +162,10 @@ CUresult encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank,
 //    and costs a zero fill of C and reduce-adds, so every tile is owned whole
 //    by one CTA (one per tile, or one per SM walking several); 128-wide
 //    tiles give more of them;
-//  * otherwise one CTA per SM shares the (tile, slab) units; 256 columns per
-//    tile halve the L2->SM traffic of A against 128, and 256 rows (two MMAs
-//    on one B stage) pay off once there are 16 or more 128-row tiles (a
-//    4096 x 4096 x 4096 layer: 100 us against 105 us; a 512-row layer runs
-//    faster with 128 rows: 23 us against 29 us).
+//  * otherwise 256 columns per tile (half the L2 -> SM traffic of A against
+//    128) and either 256 rows when each CTA gets enough K work, or 128 rows
+//    with one tile per CTA when the tiles nearly fill the GPU, or 128 rows
+//    with the (tile, slab) units shared by one CTA per SM (stream-K).
 void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, int* ctas_out,
                   int* mc_out) {
   const int64_t slabs = (K + 63) / 64;
@@ -180,8 +179,25 @@ void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, i
     return;
   }
   *TN_out = N > 128 ? 256 : 128;
-  *mc_out = n_tiles >= 16 ? 256 : 128;
-  *ctas_out = sms;
+  const int64_t ntn = (N + *TN_out - 1) / *TN_out;
+  // 256-row tiles (two MMAs per B stage: a third less L2 -> SM traffic per
+  // flop, eight MMAs per ring step) hold their accumulator in all of TMEM,
+  // so the 256 KB epilogue of a CTA (~28 B/clk per SM through the TMA store
+  // path) overlaps no MMAs.  They pay when each CTA has enough K work to
+  // amortise it: ~20 double slabs or more (1024x4096x4096: 33.7 against
+  // 37.5 us; 512x4608x3136, 12 per CTA: 26.9 against 23.0 us).
+  const int64_t pair_units = (n_tiles + 1) / 2 * ntn * slabs;
+  if (pair_units >= 20LL * sms) {
+    *mc_out = 256;
+    *ctas_out = sms;
+    return;
+  }
+  *mc_out = 128;
+  // one whole tile per CTA when the tiles nearly fill the GPU (no K split:
+  // no zero fill of C, no reductions, a store epilogue; 2048^3: 21.4 against
+  // 23.7 us), else stream-K over every SM
+  const int64_t tiles = n_tiles * ntn;
+  *ctas_out = (4 * tiles >= 3 * (int64_t)sms && tiles <= sms) ? (int)tiles : sms;
 }
 
 // Density (per mille) from which a 128-row tile runs on the tensor cores.

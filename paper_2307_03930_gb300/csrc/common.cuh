@@ -79,15 +79,23 @@ __device__ __forceinline__ unsigned long long wait_limit_ns(const int* status) {
 
 // Wait for the phase with the given parity to complete.  Gives up after the
 // device's wait limit, records kStatusTimeout in *status and returns false.
+// The clock and the limit (a global load) are first read after 256 polls,
+// so a wait that ends soon touches no memory: a pipeline stage that is
+// waited on every iteration must not pay an L2 round trip each time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
   if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  const unsigned long long limit = wait_limit_ns(status);
+  unsigned long long t0 = 0, limit = 0;
   for (uint32_t spin = 1;; ++spin) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((spin & 255u) == 0 && global_ns() - t0 > limit) {
-      if (status) atomicOr(status, kStatusTimeout);
-      return false;
+    if ((spin & 255u) == 0) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) {
+        t0 = now;
+        limit = wait_limit_ns(status);
+      } else if (now - t0 > limit) {
+        if (status) atomicOr(status, kStatusTimeout);
+        return false;
+      }
     }
   }
 }

@@ -11,7 +11,13 @@
 //
 // Warp roles: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2.. =
 // epilogue (warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31; with 8
-// epilogue warps two share a lane quarter and split its columns).
+// epilogue warps two share a lane quarter and split its columns).  The
+// producer and MMA warps wait as whole warps (converged) and one lane
+// issues.  Each ring step costs such a warp a few hundred cycles (measured:
+// a wait on a completed mbarrier, an arrive or a commit, and the wake-up of
+// the other side), about the 512 tensor-pipe cycles of the four MMAs of a
+// 128-row K slab, so with 128-row tiles both warps move two stages per step
+// (the producer's two lanes issue their stages' copies side by side).
 //
 // Schedule: persistent stream-K.  The (tile, K slab) units of all dense tiles
 // are cut into one equal contiguous share per SM, so small-M problems (few
@@ -87,8 +93,13 @@ struct DenseTable {
 };
 
 // Stream-K split of the (tile, K slab) units: CTA b owns [b U / G, (b+1) U / G).
+// U < 2^31 and b <= G < 2^16 (checked on the host), so floor(U b / G) is
+// (U / G) b + ((U % G) b) / G in 32-bit unsigned divisions (a 64-bit
+// division is a long software sequence that every CTA would pay at start).
 __device__ __forceinline__ int64_t unit_begin(int64_t U, int64_t b, int64_t G) {
-  return U * b / G;
+  const uint32_t u = (uint32_t)U, g = (uint32_t)G, bb = (uint32_t)b;
+  const uint32_t q = u / g, r = u - q * g;
+  return (int64_t)q * bb + (int64_t)((r * bb) / g);
 }
 
 // Advance the problem index q (monotone in u) so that u belongs to problem q.
@@ -103,8 +114,8 @@ __device__ __forceinline__ int64_t tile_boundary(const DenseTable<NP>& T, int64_
   if (x >= T.units) return T.units;
   int q = 0;
   advance_problem(T, x, q);
-  const int64_t slabs = T.p[q].slabs;
-  const int64_t r = (x - T.p[q].unit0) % slabs;
+  const uint32_t slabs = (uint32_t)T.p[q].slabs;
+  const uint32_t r = (uint32_t)(x - T.p[q].unit0) % slabs;
   return r ? x + (slabs - r) : x;
 }
 
@@ -114,6 +125,8 @@ __device__ __forceinline__ int64_t tile_boundary(const DenseTable<NP>& T, int64_
 struct Cursor {
   int q, mt, nt, slab;
   int mtiles, ntiles, slabs;
+  int b3d;   // problem q's B tensor map is 3-D (kept in a register: the
+             // parameter table is indexed by q, a run-time value)
 };
 
 template <int NP, int MH>
@@ -122,6 +135,7 @@ __device__ __forceinline__ void cursor_load(const DenseTable<NP>& T, Cursor& c) 
   c.mtiles = (P.n_copy + MH - 1) / MH;
   c.ntiles = P.n_ntiles;
   c.slabs = P.slabs;
+  c.b3d = P.b3d;
 }
 
 template <int NP, int MH>
@@ -130,11 +144,11 @@ __device__ __forceinline__ Cursor cursor_at(const DenseTable<NP>& T, int64_t u) 
   c.q = 0;
   advance_problem(T, u, c.q);
   cursor_load<NP, MH>(T, c);
-  const int64_t lu = u - T.p[c.q].unit0;
-  const int64_t tile = lu / c.slabs;
-  c.slab = (int)(lu - tile * c.slabs);
-  c.nt = (int)(tile / c.mtiles);
-  c.mt = (int)(tile - (int64_t)c.nt * c.mtiles);
+  const uint32_t lu = (uint32_t)(u - T.p[c.q].unit0);
+  const uint32_t tile = lu / (uint32_t)c.slabs;
+  c.slab = (int)(lu - tile * (uint32_t)c.slabs);
+  c.nt = (int)(tile / (uint32_t)c.mtiles);
+  c.mt = (int)(tile - (uint32_t)c.nt * (uint32_t)c.mtiles);
   return c;
 }
 
@@ -218,109 +232,167 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     // ---------------- TMA producer -----------------------------------------
-    if (lane == 0) {
-      int64_t i = 0;
-      int st = 0;
-      uint32_t ph = 0;   // ring stage and its phase parity
-      bool ok = true;
-      Cursor c = cursor_at<NP, MH>(T, u0);
-      for (int64_t u = u0; u < u1; ++u, ++i) {
-        if (i >= S && !mbar_wait_bounded(&empty[st], ph ^ 1u, T.status)) {
-          ok = false;
-          break;
-        }
-        const DenseProb& P = T.p[c.q];
-        uint8_t* a_dst = smem + (size_t)st * kStageBytes;
+    // The whole warp walks the ring (waits are warp-wide, so the warp stays
+    // converged); lane 0 issues the copies.
+    int64_t i = 0;
+    int st = 0;
+    uint32_t ph = 0;   // ring stage and its phase parity
+    bool ok = true;
+    Cursor c = cursor_at<NP, MH>(T, u0);
+    // two stages per iteration (the MMA warp takes them in pairs too): each
+    // ring step costs this warp a few hundred cycles
+    constexpr int kPair = MH == 1 ? 2 : 1;
+    for (int64_t u = u0; u < u1;) {
+      const int n = (kPair == 2 && u + 1 < u1) ? 2 : 1;
+      const int st2 = st + 1 == S ? 0 : st + 1;
+      const uint32_t ph2 = st + 1 == S ? ph ^ 1u : ph;
+      bool got = i < S || mbar_wait_bounded(&empty[st], ph ^ 1u, T.status);
+      if (n == 2 && i + 1 >= S) got = got && mbar_wait_bounded(&empty[st2], ph2 ^ 1u, T.status);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      // lane j fills stage j of the pair: the two stages' copies are issued
+      // by one instruction stream, side by side
+      Cursor c1 = c;
+      cursor_next<NP, MH>(T, c1);
+      if (lane < n) {
+        const Cursor& cj = lane ? c1 : c;
+        const int sj = lane ? st2 : st;
+        uint8_t* a_dst = smem + (size_t)sj * kStageBytes;
         uint8_t* b_dst = a_dst + MH * kABytes;
-        const int k0 = c.slab * kTK;
-        mbar_arrive_expect_tx(&full[st], kStageBytes);
+        const int k0 = cj.slab * kTK;
+        mbar_arrive_expect_tx(&full[sj], kStageBytes);
         // A: one box of MH x 128 rows (rows past the last copy are zero-filled)
-        tma_load_2d(a_dst, &T.tmA[c.q], k0, c.mt * MH * kTM, &full[st]);
+        tma_load_2d(a_dst, &T.tmA[cj.q], k0, cj.mt * MH * kTM, &full[sj]);
         // B: TN / 64 chunks of 64 columns, one 3-D box when N is a multiple
         // of 64 (x = column in chunk, y = k, z = chunk), else one 2-D box each
-        if (P.b3d) {
-          tma_load_3d(b_dst, &T.tmB[c.q], 0, k0, c.nt * (TN / 64), &full[st]);
+        if (cj.b3d) {
+          tma_load_3d(b_dst, &T.tmB[cj.q], 0, k0, cj.nt * (TN / 64), &full[sj]);
         } else {
 #pragma unroll
-          for (int j = 0; j < TN / 64; ++j)
-            tma_load_2d(b_dst + j * (kTK * 128), &T.tmB[c.q], c.nt * TN + 64 * j, k0, &full[st]);
+          for (int jj = 0; jj < TN / 64; ++jj)
+            tma_load_2d(b_dst + jj * (kTK * 128), &T.tmB[cj.q], cj.nt * TN + 64 * jj, k0,
+                        &full[sj]);
         }
-        // row tiles fastest: CTAs that run together share B in L2
+      }
+      // row tiles fastest: CTAs that run together share B in L2
+      if (n == 2) {
+        c = c1;
         cursor_next<NP, MH>(T, c);
+      } else {
+        c = c1;
+      }
+      __syncwarp();
+      for (int j = 0; j < n; ++j) {
         if (++st == S) {
           st = 0;
           ph ^= 1u;
         }
       }
-      if (!ok) {
-        // consumers gave up: wait (bounded) for our copies in flight to land
-        for (int64_t j = (i > S ? i - S : 0); j < i; ++j)
-          mbar_wait_bounded(&full[j % S], (uint32_t)(j / S) & 1u, T.status);
-      }
+      u += n;
+      i += n;
+    }
+    if (!ok && lane == 0) {
+      // consumers gave up: wait (bounded) for our copies in flight to land
+      for (int64_t j = (i > S ? i - S : 0); j < i; ++j)
+        mbar_wait_bounded(&full[j % S], (uint32_t)(j / S) & 1u, T.status);
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer (one thread) --------------------------------
-    if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, TN, false, true);
-      int seg = -1;
-      int st = 0;
-      uint32_t ph = 0;
-      bool ok = true;
-      Cursor c = cursor_at<NP, MH>(T, u0);
-      int bsel = NBUF - 1;      // accumulator set of the current segment
-      uint32_t bph = 1;         // its acc_empty parity (flips each reuse)
-      for (int64_t u = u0; u < u1 && ok; ++u) {
-        const int slab = c.slab;
-        const int kc = T.kchunk;
-        const bool first = (u == u0) || slab == 0 || (kc && slab % kc == 0);
-        const bool last = (u + 1 == u1) || slab + 1 == c.slabs || (kc && (slab + 1) % kc == 0);
-        if (first) {
-          ++seg;
-          if (++bsel == NBUF) {
-            bsel = 0;
-            bph ^= 1u;
-          }
-          // the epilogue must have drained this accumulator (segment seg - NBUF)
-          if (seg >= NBUF && !mbar_wait_bounded(&acc_empty[bsel], bph ^ 1u, T.status)) {
-            ok = false;
-            break;
-          }
-          tc::fence_after_sync();
+    // ---------------- MMA issuer --------------------------------------------
+    // The warp waits together; lane 0 issues the MMAs and the commits.  The
+    // smem descriptors of stage 0 are built once; stage s, K step kk and
+    // half hh only move the start address (a 14-bit field in 16-byte units:
+    // shared memory is below 256 KB, so the sum never carries out of it).
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTM, TN, false, true);
+    const uint32_t sbase = smem_u32(smem);
+    // A: K-major, 128-byte swizzle, 8-row groups 1024 B apart; a K step of
+    // 16 BF16 is 32 bytes inside the swizzle row.  B: N-major (row k of B =
+    // 128 bytes of 64 N values), 128-byte swizzle; 64-wide N chunks are
+    // 64 rows x 128 B = 8 KB apart (LBO), 8-row K groups 1024 B apart (SBO);
+    // a K step of 16 rows = 2 KB.
+    const uint64_t a_desc0 = tc::smem_desc(sbase, 16, 1024, 2);
+    const uint64_t b_desc0 = tc::smem_desc(sbase + MH * kABytes, kTK * 128, 1024, 2);
+    int seg = -1;
+    int st = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    Cursor c = cursor_at<NP, MH>(T, u0);
+    int bsel = NBUF - 1;      // accumulator set of the current segment
+    uint32_t bph = 1;         // its acc_empty parity (flips each reuse)
+    const int kc = T.kchunk;
+    // 128-row tiles: two K slabs per iteration when both belong to the same
+    // accumulator segment.  Every ring step (a wait on a full stage, a
+    // commit) costs this warp a few hundred cycles, about what the four MMAs
+    // of one 128-row slab take on the tensor pipe.  (A 256-row stage already
+    // holds eight MMAs; pairing its three stages would leave the ring too
+    // shallow to cover the commit -> producer -> consumer round trip.)
+    constexpr int kPair = MH == 1 ? 2 : 1;
+    auto seg_end_after = [&](int64_t uu, int sl) {
+      return (uu + 1 == u1) || sl + 1 == c.slabs || (kc && (sl + 1) % kc == 0);
+    };
+    for (int64_t u = u0; u < u1;) {
+      const int slab = c.slab;
+      const bool first = (u == u0) || slab == 0 || (kc && slab % kc == 0);
+      const bool end1 = seg_end_after(u, slab);
+      const int n = (end1 || kPair == 1) ? 1 : 2;   // slabs this iteration
+      const bool last = n == 1 ? end1 : seg_end_after(u + 1, slab + 1);
+      if (first) {
+        ++seg;
+        if (++bsel == NBUF) {
+          bsel = 0;
+          bph ^= 1u;
         }
-        const uint32_t d_tmem = tmem + (uint32_t)(bsel * MH * TN);
-        if (!mbar_wait_bounded(&full[st], ph, T.status)) {
+        // the epilogue must have drained this accumulator (segment seg - NBUF)
+        if (seg >= NBUF &&
+            !__all_sync(0xffffffffu, mbar_wait_bounded(&acc_empty[bsel], bph ^ 1u, T.status))) {
           ok = false;
           break;
         }
         tc::fence_after_sync();
-        const uint32_t a_base = smem_u32(smem + (size_t)st * kStageBytes);
-        const uint32_t b_base = a_base + MH * kABytes;
+      }
+      const int st2 = st + 1 == S ? 0 : st + 1;
+      const uint32_t ph2 = st + 1 == S ? ph ^ 1u : ph;
+      bool got = mbar_wait_bounded(&full[st], ph, T.status);
+      if (n == 2) got = got && mbar_wait_bounded(&full[st2], ph2, T.status);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+      if (lane == 0) {
+        const uint32_t d_tmem = tmem + (uint32_t)(bsel * MH * TN);
 #pragma unroll
-        for (int kk = 0; kk < kTK / 16; ++kk) {
-          // B: N-major (row k of B = 128 bytes of 64 N values), 128-byte
-          // swizzle; 64-wide N chunks are 64 rows x 128 B = 8 KB apart (LBO),
-          // 8-row K groups 1024 B apart (SBO); a K step of 16 rows = 2 KB.
-          const uint64_t bd = tc::smem_desc(b_base + kk * 16 * 128, kTK * 128, 1024, 2);
+        for (int j = 0; j < 2; ++j) {
+          if (j == n) break;
+          const int sj = j ? st2 : st;
+          const uint64_t so = (uint64_t)((sj * kStageBytes) >> 4);
 #pragma unroll
-          for (int hh = 0; hh < MH; ++hh) {
-            // A: K-major, 128-byte swizzle, 8-row groups 1024 B apart; a K
-            // step of 16 BF16 is 32 bytes inside the swizzle row.
-            const uint64_t ad = tc::smem_desc(a_base + hh * kABytes + kk * 32, 16, 1024, 2);
-            tc::mma_bf16(d_tmem + hh * TN, ad, bd, idesc, (!first || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < kTK / 16; ++kk) {
+            const uint64_t bd = b_desc0 + so + (uint64_t)((kk * 16 * 128) >> 4);
+#pragma unroll
+            for (int hh = 0; hh < MH; ++hh) {
+              const uint64_t ad = a_desc0 + so + (uint64_t)((hh * kABytes + kk * 32) >> 4);
+              tc::mma_bf16(d_tmem + hh * TN, ad, bd, idesc, (!first || j > 0 || kk > 0) ? 1u : 0u);
+            }
           }
+          tc::mma_commit(&empty[sj]);               // stage free once these MMAs finish
         }
-        tc::mma_commit(&empty[st]);                 // stage free once these MMAs finish
         if (last) tc::mma_commit(&acc_full[bsel]);  // accumulator complete
+      }
+      __syncwarp();
+      for (int j = 0; j < n; ++j) {
         cursor_next<NP, MH>(T, c);
         if (++st == S) {
           st = 0;
           ph ^= 1u;
         }
       }
-      if (!ok) {
-        // make the epilogue's waits end: release every accumulator it expects
-        for (int b = 0; b < NBUF; ++b) tc::mma_commit(&acc_full[b]);
-      }
+      u += n;
+    }
+    if (!ok && lane == 0) {
+      // make the epilogue's waits end: release every accumulator it expects
+      for (int b = 0; b < NBUF; ++b) tc::mma_commit(&acc_full[b]);
     }
   } else {
     // ---------------- epilogue: TMEM -> registers -> C -----------------------
@@ -346,15 +418,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         b = 0;
         bph ^= 1u;
       }
-      const bool ok = mbar_wait_bounded(&acc_full[b], bph, T.status);
-      tc::fence_after_sync();
-      const int64_t n0 = (int64_t)nt * TN;
-      const bool add = !whole || P.accumulate;
-#pragma unroll 1
+      // the tiles' C rows, fetched while the MMAs run
+      int32_t trow[MH];
+#pragma unroll
       for (int hh = 0; hh < MH; ++hh) {
         const int copy = mt * MH + hh;
-        if (copy >= P.n_copy) break;   // warp-uniform
-        const int64_t row0 = (int64_t)__ldg(&P.tile_order[copy]) * kTM + quarter * 32;
+        trow[hh] = copy < P.n_copy ? __ldg(&P.tile_order[copy]) : 0;
+      }
+      // the problem's scalars in registers for the chunk loop
+      const int64_t PM = P.M, PN = P.N;
+      const int n_copy = P.n_copy, tma_c = P.tma_c, out_i32 = T.out_i32;
+      const bool add = !whole || P.accumulate;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&acc_full[b], bph, T.status));
+      tc::fence_after_sync();
+      const int64_t n0 = (int64_t)nt * TN;
+#pragma unroll
+      for (int hh = 0; hh < MH; ++hh) {
+        const int copy = mt * MH + hh;
+        if (copy >= n_copy) break;   // warp-uniform
+        const int64_t row0 = (int64_t)trow[hh] * kTM + quarter * 32;
 #pragma unroll 1
         for (int cc = part * (TN / 32 / kParts); cc < (part + 1) * (TN / 32 / kParts); ++cc) {
           uint32_t r[32];
@@ -363,13 +445,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                                  r);
           tc::tmem_ld_wait();
           const int64_t col0 = n0 + cc * 32;
-          if (!ok || row0 >= P.M || col0 >= P.N) continue;   // warp-uniform
-          if (T.out_i32) {
+          if (!ok || row0 >= PM || col0 >= PN) continue;   // warp-uniform
+          if (out_i32) {
             // an exact integer in FP32 (|partial| < 2^24): convert to INT32
 #pragma unroll
             for (int j = 0; j < 32; ++j) r[j] = (uint32_t)__float2int_rn(__uint_as_float(r[j]));
           }
-          if (P.tma_c) {
+          if (tma_c) {
             // staging tile (chunk & 1) is free once the copy issued two
             // chunks ago has read it
             uint8_t* buf = my_stage + (size_t)(chunk % kStagePerWarp) * kStageC;
@@ -405,13 +487,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < 32; ++j) tr[lane * 32 + ((j + lane) & 31)] = __uint_as_float(r[j]);
           __syncwarp();
           const int64_t col = col0 + lane;
-          const int rows = (int)(P.M - row0 < 32 ? P.M - row0 : 32);
-          if (col < P.N) {
+          const int rows = (int)(PM - row0 < 32 ? PM - row0 : 32);
+          if (col < PN) {
 #pragma unroll 4
             for (int rr = 0; rr < rows; ++rr) {
               const float v = tr[rr * 32 + ((lane + rr) & 31)];
               float* dst = P.C + (row0 + rr) * P.ldc + col;
-              if (T.out_i32) {
+              if (out_i32) {
                 int* di = reinterpret_cast<int*>(dst);
                 const int iv = (int)__float_as_uint(v);   // already converted
                 if (add) atomicAdd(di, iv);
@@ -537,7 +619,8 @@ constexpr int64_t kMinUnitsPerCta = 8;
 // CTAs of a launch over `units` (tile, slab) units in `tiles` tiles: one per
 // SM at most, and no stream-K piece shorter than kMinUnitsPerCta slabs.
 static int64_t grid_for(int64_t units, int64_t tiles, int ctas) {
-  int64_t G = std::min<int64_t>(ctas, units);
+  // (the kernel's 32-bit split arithmetic wants G < 2^16)
+  int64_t G = std::min<int64_t>(std::min(ctas, 65535), units);
   if (!use_aligned(tiles, G)) G = std::min<int64_t>(G, std::max(tiles, units / kMinUnitsPerCta));
   return std::max<int64_t>(1, G);
 }
@@ -574,6 +657,8 @@ rosko_status run_jobs(const DenseJob* jobs, int count, int ctas, cudaStream_t st
     ++n;
   }
   if (n == 0) return ROSKO_OK;
+  // the kernel splits and walks units in 32-bit arithmetic
+  if (units >= (int64_t(1) << 31)) return ROSKO_ERR_UNSUPPORTED;
   T.count = n;
   T.units = units;
   int64_t tiles = 0;

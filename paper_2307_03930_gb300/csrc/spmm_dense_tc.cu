@@ -193,6 +193,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // one thread fills ring stage sj with unit cj: A (MH x 128 rows; rows past
+  // the last copy are zero-filled) and TN / 64 chunks of 64 B columns, one
+  // 3-D box when N is a multiple of 64 (x = column in chunk, y = k,
+  // z = chunk), else one 2-D box each
+  auto issue_stage = [&](const Cursor& cj, int sj) {
+    uint8_t* a_dst = smem + (size_t)sj * kStageBytes;
+    uint8_t* b_dst = a_dst + MH * kABytes;
+    const int k0 = cj.slab * kTK;
+    mbar_arrive_expect_tx(&full[sj], kStageBytes);
+    tma_load_2d(a_dst, &T.tmA[cj.q], k0, cj.mt * MH * kTM, &full[sj]);
+    if (cj.b3d) {
+      tma_load_3d(b_dst, &T.tmB[cj.q], 0, k0, cj.nt * (TN / 64), &full[sj]);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < TN / 64; ++jj)
+        tma_load_2d(b_dst + jj * (kTK * 128), &T.tmB[cj.q], cj.nt * TN + 64 * jj, k0, &full[sj]);
+    }
+  };
   int64_t u0 = unit_begin(T.units, blockIdx.x, gridDim.x);
   int64_t u1 = unit_begin(T.units, blockIdx.x + 1, gridDim.x);
   if (T.aligned) {
@@ -220,6 +238,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&acc_empty[b], kEpiWarps);
     }
     fence_barrier_init();
+    // the first ring fill goes out now: its (cold, DRAM) latency overlaps
+    // the TMEM allocation and the block barrier
+    Cursor c = cursor_at<NP, MH>(T, u0);
+    for (int64_t u = u0; u < u1 && u < u0 + S; ++u) {
+      issue_stage(c, (int)(u - u0));
+      cursor_next<NP, MH>(T, c);
+    }
   }
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, NBUF * MH * TN);
@@ -234,15 +259,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- TMA producer -----------------------------------------
     // The whole warp walks the ring (waits are warp-wide, so the warp stays
     // converged); lane 0 issues the copies.
-    int64_t i = 0;
-    int st = 0;
-    uint32_t ph = 0;   // ring stage and its phase parity
+    // the first min(S, units) stages were filled at start
+    const int64_t pre = std::min<int64_t>(S, u1 - u0);
+    int64_t i = pre;
+    int st = (int)(pre % S);
+    uint32_t ph = pre == S ? 1u : 0u;   // ring stage and its phase parity
     bool ok = true;
-    Cursor c = cursor_at<NP, MH>(T, u0);
+    Cursor c = cursor_at<NP, MH>(T, u0 + pre < u1 ? u0 + pre : u0);
     // two stages per iteration (the MMA warp takes them in pairs too): each
     // ring step costs this warp a few hundred cycles
     constexpr int kPair = MH == 1 ? 2 : 1;
-    for (int64_t u = u0; u < u1;) {
+    for (int64_t u = u0 + pre; u < u1;) {
       const int n = (kPair == 2 && u + 1 < u1) ? 2 : 1;
       const int st2 = st + 1 == S ? 0 : st + 1;
       const uint32_t ph2 = st + 1 == S ? ph ^ 1u : ph;
@@ -256,26 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // by one instruction stream, side by side
       Cursor c1 = c;
       cursor_next<NP, MH>(T, c1);
-      if (lane < n) {
-        const Cursor& cj = lane ? c1 : c;
-        const int sj = lane ? st2 : st;
-        uint8_t* a_dst = smem + (size_t)sj * kStageBytes;
-        uint8_t* b_dst = a_dst + MH * kABytes;
-        const int k0 = cj.slab * kTK;
-        mbar_arrive_expect_tx(&full[sj], kStageBytes);
-        // A: one box of MH x 128 rows (rows past the last copy are zero-filled)
-        tma_load_2d(a_dst, &T.tmA[cj.q], k0, cj.mt * MH * kTM, &full[sj]);
-        // B: TN / 64 chunks of 64 columns, one 3-D box when N is a multiple
-        // of 64 (x = column in chunk, y = k, z = chunk), else one 2-D box each
-        if (cj.b3d) {
-          tma_load_3d(b_dst, &T.tmB[cj.q], 0, k0, cj.nt * (TN / 64), &full[sj]);
-        } else {
-#pragma unroll
-          for (int jj = 0; jj < TN / 64; ++jj)
-            tma_load_2d(b_dst + jj * (kTK * 128), &T.tmB[cj.q], cj.nt * TN + 64 * jj, k0,
-                        &full[sj]);
-        }
-      }
+      if (lane < n) issue_stage(lane ? c1 : c, lane ? st2 : st);
       // row tiles fastest: CTAs that run together share B in L2
       if (n == 2) {
         c = c1;

@@ -167,7 +167,7 @@ CUresult encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, cuuint32_t rank,
 //    with one tile per CTA when the tiles nearly fill the GPU, or 128 rows
 //    with the (tile, slab) units shared by one CTA per SM (stream-K).
 void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, int* ctas_out,
-                  int* mc_out) {
+                  int* mc_out, bool chunked) {
   const int64_t slabs = (K + 63) / 64;
   if (slabs < 16) {
     const int64_t tiles = n_tiles * ((N + 127) / 128);
@@ -186,8 +186,11 @@ void dense_config(int64_t n_tiles, int64_t N, int64_t K, int sms, int* TN_out, i
   // path) overlaps no MMAs.  They pay when each CTA has enough K work to
   // amortise it: ~20 double slabs or more (1024x4096x4096: 33.7 against
   // 37.5 us; 512x4608x3136, 12 per CTA: 26.9 against 23.0 us).
+  // (INT8 codes drain the accumulator every 1,024 K: that needs the second
+  // TMEM set to overlap the drains, so their tiles stay 128 rows high;
+  // 11008x4096x2048 at 90 %: 205 against 268 us)
   const int64_t pair_units = (n_tiles + 1) / 2 * ntn * slabs;
-  if (pair_units >= 20LL * sms) {
+  if (!chunked && pair_units >= 20LL * sms) {
     *mc_out = 256;
     *ctas_out = sms;
     return;
@@ -292,7 +295,7 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
   }
   int TN = 256, ds = 1;
   int mc = 128;
-  dense_config((M + 127) / 128, N, K, sms, &TN, &ds, &mc);
+  dense_config((M + 127) / 128, N, K, sms, &TN, &ds, &mc, dt == ROSKO_I8);
   t->dense_n_r = TN;
   t->dense_split_k = ds;
   t->dense_m_c = mc;
@@ -524,7 +527,7 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
     if (t.dense_m_c != 128 && t.dense_m_c != 256) return ROSKO_ERR_INVALID_ARG;
     if (!tile || tile->dense_n_r <= 0 || tile->dense_split_k <= 0 || tile->dense_m_c <= 0) {
       int TN = 256, ds = 1, mc = 128;
-      dense_config(n_dense, N, A->K, sms, &TN, &ds, &mc);
+      dense_config(n_dense, N, A->K, sms, &TN, &ds, &mc, p == ROSKO_I8);
       if (!tile || tile->dense_n_r <= 0) t.dense_n_r = TN;
       if (!tile || tile->dense_split_k <= 0) t.dense_split_k = ds;
       if (!tile || tile->dense_m_c <= 0) t.dense_m_c = mc;
@@ -620,20 +623,26 @@ rosko_status spmm_run(rosko_packed_s* A, const void* B_dev, rosko_dtype b_dtype,
     }
     return ROSKO_OK;
   }
-  if (zero_c && !(flags & kRunZeroed) &&
+  // the zero fill runs under the tensor-core launch when there is one (a
+  // small kernel it depends on programmatically), else as a memset
+  const bool run_dense = n_dense > 0 && !skip_dense;
+  const bool fill = zero_c && !(flags & kRunZeroed);
+  const ZeroFill zf{C_dev, ldc * (int64_t)csz, N * (int64_t)csz, A->M};
+  if (fill && !run_dense &&
       cudaMemset2DAsync(C_dev, (size_t)ldc * csz, 0, (size_t)N * csz, (size_t)A->M, st) !=
           cudaSuccess)
     return ROSKO_ERR_CUDA;
-  if (n_dense > 0 && !skip_dense) {
+  if (run_dense) {
+    const ZeroFill* z = fill ? &zf : nullptr;
     rosko_status s =
         p == ROSKO_I8
             ? dense_spmm_i8_launch(A, n_dense, static_cast<const int8_t*>(B_dev), N, ldb,
                                    static_cast<int32_t*>(C_dev), ldc, t.dense_n_r,
-                                   t.dense_split_k, t.dense_m_c / 128, st)
+                                   t.dense_split_k, t.dense_m_c / 128, z, st)
             : dense_spmm_launch(A->dense_A, A->n_copy * 128, A->Kpad, A->tile_order_dev, n_dense,
                                 A->K, B_dev, N, ldb, static_cast<float*>(C_dev), ldc, A->M,
                                 accumulate, t.dense_n_r, t.dense_split_k, t.dense_m_c / 128,
-                                zero_c, st);
+                                zero_c, z, st);
     if (s != ROSKO_OK) return s;
   }
   if (L.order == 3) {
@@ -716,7 +725,7 @@ rosko_status spmm_batched_impl(int32_t count, rosko_packed_s* const* A, const vo
       j.M = A[i]->M;
       j.accumulate = accumulate;
       int tn = 256, ds = 1, mc = 128;
-      dense_config(nd, N[i], A[i]->K, sms, &tn, &ds, &mc);
+      dense_config(nd, N[i], A[i]->K, sms, &tn, &ds, &mc, false);
       if (tiles && tiles[i].dense_n_r > 0) tn = tiles[i].dense_n_r;
       if (tiles && tiles[i].dense_m_c > 0) mc = tiles[i].dense_m_c;
       if ((tn != 128 && tn != 256) || (mc != 128 && mc != 256)) return ROSKO_ERR_INVALID_ARG;

@@ -170,11 +170,19 @@ bool sparse_config_supported(rosko_dtype p_dt, rosko_dtype b_dt, rosko_dtype c_d
 int sparse_default_V(rosko_dtype p_dt, int R, int order);
 
 // spmm_dense_tc.cu
+// A zero fill of C (rows x row_bytes at `pitch` bytes) issued right before a
+// tensor-core launch: a small kernel that lets the tensor-core launch start
+// at once (programmatic dependent launch); only that kernel's epilogue waits
+// for the fill, so the fill runs under its MMAs.
+struct ZeroFill {
+  void* C;
+  int64_t pitch, row_bytes, rows;
+};
 rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t Kpad,
                                const int32_t* tile_order_dev, int64_t n_tiles, int64_t K,
                                const void* B, int64_t N, int64_t ldb, float* C, int64_t ldc,
                                int64_t M, int accumulate, int TN, int ctas, int MH,
-                               bool c_zeroed,
+                               bool c_zeroed, const ZeroFill* zf,
                                cudaStream_t st);
 // One row-direct (order 4) sparse SpMM of a batch: the panels of h listed in
 // panel_list (NULL: all rows), B and C of this problem.
@@ -219,6 +227,7 @@ struct DenseJob {
   int accumulate;
   int kchunk = 0;    // K slabs per exact-integer chunk (INT8 codes), 0: none
   int out_i32 = 0;   // C is INT32 (INT8 codes through the BF16 pipe)
+  int pdl = 0;       // launch as a programmatic dependent of the previous kernel
 };
 // INT8 x INT8 -> INT32 through the BF16 tensor pipe: B is converted to BF16
 // (exact) in stream-ordered scratch, the handle's dense copies hold the INT8
@@ -226,7 +235,7 @@ struct DenseJob {
 // and added into C, which the caller has zeroed unless it accumulates.
 rosko_status dense_spmm_i8_launch(const rosko_packed_s* h, int64_t n_tiles, const int8_t* B,
                                   int64_t N, int64_t ldb, int32_t* C, int64_t ldc, int TN,
-                                  int ctas, int MH, cudaStream_t st);
+                                  int ctas, int MH, const ZeroFill* zf, cudaStream_t st);
 // One persistent stream-K launch over all jobs' dense tiles (count <= 64);
 // C of jobs whose tiles the split cuts must be zeroed by the caller unless
 // they accumulate (dense_batch_needs_zero).

@@ -404,6 +404,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------- epilogue: TMEM -> registers -> C -----------------------
+    // C may still be being zero-filled by the kernel this launch depends on
+    // (programmatic dependent launch): wait for it before any write to C.
+    // Without such a dependency the wait returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int quarter = warp & 3;                  // TMEM lanes 32 quarter .. + 31
     const int part = (warp - 2) >> 2;              // column part of this warp
     constexpr int kParts = kEpiWarps / 4;
@@ -549,7 +553,7 @@ constexpr int dense_stages() {
 int64_t slabs_of(int64_t K) { return (K + kTK - 1) / kTK; }
 
 template <int TN, int NP, int MH>
-rosko_status launch_table(DenseTable<NP>& T, int64_t grid, cudaStream_t st) {
+rosko_status launch_table(DenseTable<NP>& T, int64_t grid, bool pdl, cudaStream_t st) {
   const size_t smem = dense_smem_bytes<TN, MH>(T.stages);
   static size_t set = 0;
   auto fn = dense_panel_kernel<TN, NP, MH>;
@@ -559,7 +563,22 @@ rosko_status launch_table(DenseTable<NP>& T, int64_t grid, cudaStream_t st) {
       return ROSKO_ERR_CUDA;
     set = smem;
   }
-  fn<<<(unsigned)grid, kThreads, smem, st>>>(T);
+  if (pdl) {
+    // starts while the preceding zero fill runs; its epilogue waits for it
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, fn, T) != cudaSuccess) return ROSKO_ERR_CUDA;
+  } else {
+    fn<<<(unsigned)grid, kThreads, smem, st>>>(T);
+  }
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
 }
@@ -678,7 +697,7 @@ rosko_status run_jobs(const DenseJob* jobs, int count, int ctas, cudaStream_t st
   T.stages = dense_stages<TN, MH>();
   T.status = device_status_word();
   if (!T.status) return ROSKO_ERR_CUDA;
-  return launch_table<TN, NP, MH>(T, grid, st);
+  return launch_table<TN, NP, MH>(T, grid, jobs[0].pdl != 0, st);
 }
 
 }  // namespace
@@ -755,6 +774,42 @@ rosko_status dense_batch_launch(const DenseJob* jobs, int count, int TN, int cta
 }
 
 namespace {
+// Zero rows x row_bytes of C (pitch bytes apart), one CTA per row at a time.
+// Dependents may launch at once: they wait (griddepcontrol.wait) before
+// touching C.
+__global__ void zero_fill_kernel(char* __restrict__ C, int64_t pitch, int64_t row_bytes,
+                                 int64_t rows, int vec16) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    char* row = C + r * pitch;
+    if (vec16) {
+      uint4* p = reinterpret_cast<uint4*>(row);
+      for (int64_t i = threadIdx.x; i < row_bytes / 16; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
+    } else {
+      uint32_t* p = reinterpret_cast<uint32_t*>(row);
+      for (int64_t i = threadIdx.x; i < row_bytes / 4; i += blockDim.x) p[i] = 0u;
+    }
+  }
+}
+
+rosko_status zero_fill_launch(const ZeroFill& z, cudaStream_t st) {
+  if (z.rows <= 0 || z.row_bytes <= 0) return ROSKO_OK;
+  // every C element type is a multiple of 4 bytes
+  if ((reinterpret_cast<uintptr_t>(z.C) % 4) != 0 || z.pitch % 4 != 0 || z.row_bytes % 4 != 0)
+    return ROSKO_ERR_INVALID_ARG;
+  const int vec16 = (reinterpret_cast<uintptr_t>(z.C) % 16 == 0 && z.pitch % 16 == 0 &&
+                     z.row_bytes % 16 == 0)
+                        ? 1
+                        : 0;
+  // a grid that is resident at once, so that every CTA has signalled its
+  // dependents before the tensor-core launch needs an SM
+  const int64_t grid = std::min<int64_t>(z.rows, (int64_t)num_sms() * 4);
+  zero_fill_kernel<<<(unsigned)grid, 256, 0, st>>>(static_cast<char*>(z.C), z.pitch, z.row_bytes,
+                                                   z.rows, vec16);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+}
+
 // INT8 -> BF16 (exact: |code| <= 127), K rows of N, into rows of ldo.
 __global__ void i8_to_bf16_kernel(const int8_t* __restrict__ B, int64_t K, int64_t N, int64_t ldb,
                                   __nv_bfloat16* __restrict__ out, int64_t ldo) {
@@ -781,7 +836,7 @@ constexpr int kI8ChunkSlabs = 16;
 
 rosko_status dense_spmm_i8_launch(const rosko_packed_s* h, int64_t n_tiles, const int8_t* B,
                                   int64_t N, int64_t ldb, int32_t* C, int64_t ldc, int TN,
-                                  int ctas, int MH, cudaStream_t st) {
+                                  int ctas, int MH, const ZeroFill* zf, cudaStream_t st) {
   if (n_tiles <= 0 || N <= 0) return ROSKO_OK;
   if (TN != 128 && TN != 256) return ROSKO_ERR_INVALID_ARG;
   if (ctas <= 0) ctas = num_sms();
@@ -797,6 +852,9 @@ rosko_status dense_spmm_i8_launch(const rosko_packed_s* h, int64_t n_tiles, cons
                                             ldo);
   count_launches(1);
   rosko_status s = cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+  // the zero fill of C (after the conversion, so that B is complete when the
+  // dependent tensor-core launch starts)
+  if (s == ROSKO_OK && zf) s = zero_fill_launch(*zf, st);
   if (s == ROSKO_OK) {
     DenseJob j;
     j.dense_A = h->dense_A;
@@ -814,6 +872,7 @@ rosko_status dense_spmm_i8_launch(const rosko_packed_s* h, int64_t n_tiles, cons
     j.accumulate = 1;   // every chunk adds into the zeroed (or accumulated) C
     j.kchunk = kI8ChunkSlabs;
     j.out_i32 = 1;
+    j.pdl = zf ? 1 : 0;
     s = dense_batch_launch(&j, 1, TN, ctas, MH, st);
   }
   cudaFreeAsync(scratch, st);
@@ -824,11 +883,14 @@ rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t 
                                const int32_t* tile_order_dev, int64_t n_tiles, int64_t K,
                                const void* B, int64_t N, int64_t ldb, float* C, int64_t ldc,
                                int64_t M, int accumulate, int TN, int ctas, int MH,
-                               bool c_zeroed, cudaStream_t st) {
+                               bool c_zeroed, const ZeroFill* zf, cudaStream_t st) {
   if (n_tiles <= 0 || N <= 0) return ROSKO_OK;
   if (TN != 128 && TN != 256) return ROSKO_ERR_INVALID_ARG;
   if (ctas <= 0) ctas = num_sms();
-  if (!accumulate && !c_zeroed && dense_needs_zero(n_tiles, N, K, TN, ctas, MH)) {
+  if (zf) {
+    rosko_status s = zero_fill_launch(*zf, st);
+    if (s != ROSKO_OK) return s;
+  } else if (!accumulate && !c_zeroed && dense_needs_zero(n_tiles, N, K, TN, ctas, MH)) {
     // zero the C rows of every dense tile (tiles are disjoint row blocks)
     std::vector<int32_t> order((size_t)n_tiles);
     if (cudaMemcpyAsync(order.data(), tile_order_dev, order.size() * 4, cudaMemcpyDeviceToHost,
@@ -858,6 +920,7 @@ rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t 
   j.ldc = ldc;
   j.M = M;
   j.accumulate = accumulate;
+  j.pdl = zf ? 1 : 0;
   return dense_batch_launch(&j, 1, TN, ctas, MH, st);
 }
 

@@ -155,6 +155,19 @@ rosko_status transpose_impl(const void* A, rosko_dtype dt, int64_t M, int64_t K,
 rosko_status unpack_impl(rosko_packed_s* h, void* A_out, int64_t lda, cudaStream_t stream);
 constexpr int64_t kRowSlotMaxK = 65280;  // sentinel k = 0xFFFF stays past every slab end
 
+// A zero fill of C (rows x row_bytes at `pitch` bytes) issued right before a
+// tensor-core launch: a small kernel that lets the tensor-core launch start
+// at once (programmatic dependent launch); only its epilogue waits for the
+// fill, so the fill runs under its MMAs.  (The latency-bound row-direct
+// kernel is not launched this way: it needs every SM slot from its start,
+// and the early start measured slower than a memset ahead of it.)
+struct ZeroFill {
+  void* C;
+  int64_t pitch, row_bytes, rows;
+};
+// Launch the zero fill (a kernel whose dependents may start at once).
+rosko_status zero_fill_launch(const ZeroFill& z, cudaStream_t st);
+
 // spmm_sparse.cu
 struct SparseLaunch {
   int R, V, W, KC, stages, split;
@@ -170,14 +183,6 @@ bool sparse_config_supported(rosko_dtype p_dt, rosko_dtype b_dt, rosko_dtype c_d
 int sparse_default_V(rosko_dtype p_dt, int R, int order);
 
 // spmm_dense_tc.cu
-// A zero fill of C (rows x row_bytes at `pitch` bytes) issued right before a
-// tensor-core launch: a small kernel that lets the tensor-core launch start
-// at once (programmatic dependent launch); only that kernel's epilogue waits
-// for the fill, so the fill runs under its MMAs.
-struct ZeroFill {
-  void* C;
-  int64_t pitch, row_bytes, rows;
-};
 rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t Kpad,
                                const int32_t* tile_order_dev, int64_t n_tiles, int64_t K,
                                const void* B, int64_t N, int64_t ldb, float* C, int64_t ldc,

@@ -792,24 +792,6 @@ __global__ void zero_fill_kernel(char* __restrict__ C, int64_t pitch, int64_t ro
   }
 }
 
-rosko_status zero_fill_launch(const ZeroFill& z, cudaStream_t st) {
-  if (z.rows <= 0 || z.row_bytes <= 0) return ROSKO_OK;
-  // every C element type is a multiple of 4 bytes
-  if ((reinterpret_cast<uintptr_t>(z.C) % 4) != 0 || z.pitch % 4 != 0 || z.row_bytes % 4 != 0)
-    return ROSKO_ERR_INVALID_ARG;
-  const int vec16 = (reinterpret_cast<uintptr_t>(z.C) % 16 == 0 && z.pitch % 16 == 0 &&
-                     z.row_bytes % 16 == 0)
-                        ? 1
-                        : 0;
-  // a grid that is resident at once, so that every CTA has signalled its
-  // dependents before the tensor-core launch needs an SM
-  const int64_t grid = std::min<int64_t>(z.rows, (int64_t)num_sms() * 4);
-  zero_fill_kernel<<<(unsigned)grid, 256, 0, st>>>(static_cast<char*>(z.C), z.pitch, z.row_bytes,
-                                                   z.rows, vec16);
-  count_launches(1);
-  return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
-}
-
 // INT8 -> BF16 (exact: |code| <= 127), K rows of N, into rows of ldo.
 __global__ void i8_to_bf16_kernel(const int8_t* __restrict__ B, int64_t K, int64_t N, int64_t ldb,
                                   __nv_bfloat16* __restrict__ out, int64_t ldo) {
@@ -828,6 +810,24 @@ __global__ void i8_to_bf16_kernel(const int8_t* __restrict__ B, int64_t K, int64
   }
 }
 }  // namespace
+
+rosko_status zero_fill_launch(const ZeroFill& z, cudaStream_t st) {
+  if (z.rows <= 0 || z.row_bytes <= 0) return ROSKO_OK;
+  // every C element type is a multiple of 4 bytes
+  if ((reinterpret_cast<uintptr_t>(z.C) % 4) != 0 || z.pitch % 4 != 0 || z.row_bytes % 4 != 0)
+    return ROSKO_ERR_INVALID_ARG;
+  const int vec16 = (reinterpret_cast<uintptr_t>(z.C) % 16 == 0 && z.pitch % 16 == 0 &&
+                     z.row_bytes % 16 == 0)
+                        ? 1
+                        : 0;
+  // a grid that is resident at once, so that every CTA has signalled its
+  // dependents before the tensor-core launch needs an SM
+  const int64_t grid = std::min<int64_t>(z.rows, (int64_t)num_sms() * 4);
+  zero_fill_kernel<<<(unsigned)grid, 256, 0, st>>>(static_cast<char*>(z.C), z.pitch, z.row_bytes,
+                                                   z.rows, vec16);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? ROSKO_OK : ROSKO_ERR_CUDA;
+}
 
 // K slabs of 64 per exact chunk: 16 slabs = 1024 products of magnitude
 // <= 127^2, so a partial sum stays below 1024 * 16129 < 2^24 and is exact in

@@ -24,9 +24,9 @@ def _run(rosko, A, B, tile, rows=None, accumulate=False, C0=None, dense_min_pm=0
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
     if C0 is not None:
         C.copy_(torch.from_numpy(C0))
-    # a zero fill of C ahead of the tensor-core launch is one small kernel
-    # (the tensor-core launch depends on it programmatically); it is counted
-    # apart from the product's launches
+    # a zero fill of C ahead of a tensor-core launch is one small kernel (the
+    # tensor-core launch depends on it programmatically); it is counted apart
+    # from the product's launches (without one, the fill is a memset)
     pl = rosko.rosko_spmm_plan(h, Bd, C, tile=tile, accumulate=accumulate)
     fill = 1 if (pl["zero_fill"] and pl["dense_tiles"] > 0) else 0
     l0 = rosko.rosko_kernel_launches()

@@ -43,8 +43,9 @@ def test_autotune_choice_is_cached_and_correct():
     i_best = int(np.argmin([t if t is not None else np.inf for t in times]))
     cand = rosko.rosko_candidate(h, 500, i_best)
     assert cand.as_dict() == best.as_dict()
-    # mode AUTOTUNE reuses it without searching again (no extra launches)
+    # mode AUTOTUNE reuses it without searching again (no extra launches:
+    # at most a zero fill, a tensor-core and a sparse launch)
     l0 = rosko.rosko_kernel_launches()
     rosko.rosko_spmm(h, Bd, C, tile=rosko.make_tile(mode=rosko.SCHED_AUTOTUNE))
-    assert rosko.rosko_kernel_launches() - l0 <= 2
+    assert rosko.rosko_kernel_launches() - l0 <= 3
     check("bf16", *run(rosko, A, B, "bf16", m_r=16, tile=best))

@@ -1025,10 +1025,16 @@ const SegEntry* direct_segments(const rosko_packed_s* h, const int32_t* panel_li
 // fine list (more, shorter pieces; the cut rows are added atomically).
 int direct_pick(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_panels, int64_t N,
                 int V) {
-  int64_t ns = 0;
+  int64_t ns = 0, ns_fine = 0;
   if (!direct_segments(h, panel_list, n_panels, 1, &ns, nullptr)) return 0;
   const int64_t strips = (N + 32 * V - 1) / (32 * V);
-  return ns * strips >= 4LL * 24 * num_sms() ? 1 : 0;
+  if (ns * strips >= 4LL * 24 * num_sms()) return 1;
+  // few work items: the fine list adds warps for long rows, but a cut row
+  // costs a zero fill of C and atomic adds; when cutting adds under a
+  // quarter more pieces (an even matrix with a few rows just past 64
+  // records: 512x4608 at 99 %) the rows stay whole
+  if (!direct_segments(h, panel_list, n_panels, 0, &ns_fine, nullptr)) return 1;
+  return 4 * ns_fine >= 5 * ns ? 0 : 1;
 }
 
 // Fill one problem of a row-direct table; returns the problem's block count

@@ -285,12 +285,12 @@ rosko_status schedule_analytic(int64_t M, int64_t K, int64_t N, int64_t nnz, int
     // predicted faster.  Both models are least-squares fits (relative error)
     // to the 5,000 training layers of the selector's measurement sweep
     // (M, K in [64, 4096] and convolution shapes, N in [196, 12544], 50-99.9%
-    // sparse, every schedule timed): dense ~12.4 us + 2 M K N at
-    // ~0.57 PFLOP/s, row-direct ~5.4 us + the nnz * N BF16 values it moves
+    // sparse, every schedule timed): dense ~10.8 us + 2 M K N at
+    // ~0.58 PFLOP/s, row-direct ~5.3 us + the nnz * N BF16 values it moves
     // at ~10.9 TB/s.  On the 2,000 held-out layers picking the faster path
-    // by these models costs 6% over the better of the two paths.
-    const double t_dense = 12.4 + 2.0 * (double)M * (double)K * (double)N / 0.57e15 * 1e6;
-    const double t_direct = 5.4 + (double)nnz * (double)N * 2.0 / 10.9e12 * 1e6;
+    // by these models costs 5% over the better of the two paths.
+    const double t_dense = 10.8 + 2.0 * (double)M * (double)K * (double)N / 0.58e15 * 1e6;
+    const double t_direct = 5.3 + (double)nnz * (double)N * 2.0 / 10.9e12 * 1e6;
     if (t_direct < t_dense) t->dense_split_pm = 1001;
   }
   int TN = 256, ds = 1;

@@ -28,6 +28,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Programmatic dependent launch.  pdl_wait: block until the grids this launch
+// depends on have completed and their writes are visible (at once when the
+// launch has no such dependency).  pdl_trigger: let the next launch in the
+// stream start (it waits in its own pdl_wait before touching data).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

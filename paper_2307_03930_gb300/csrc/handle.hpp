@@ -218,7 +218,8 @@ int direct_pick(const rosko_packed_s* h, const int32_t* panel_list, int64_t n_pa
 // One launch over all jobs (count <= 64, same handle / B / C types, V
 // columns per lane); C of jobs with cut rows must be zeroed by the caller
 // unless they accumulate.
-rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaStream_t st);
+rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaStream_t st,
+                                 bool pdl = false);
 // One dense-panel SpMM of a batch (see dense_batch_launch).
 struct DenseJob {
   const void* dense_A;

@@ -238,6 +238,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&acc_empty[b], kEpiWarps);
     }
     fence_barrier_init();
+    // (a programmatic dependent only of a zero fill of C, whose start means
+    // that every launch before it has completed: A and B are final here)
     // the first ring fill goes out now: its (cold, DRAM) latency overlaps
     // the TMEM allocation and the block barrier
     Cursor c = cursor_at<NP, MH>(T, u0);
@@ -402,12 +404,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       // make the epilogue's waits end: release every accumulator it expects
       for (int b = 0; b < NBUF; ++b) tc::mma_commit(&acc_full[b]);
     }
+    // every MMA is issued: the next launch in the stream may start its
+    // prologue during this CTA's epilogue
+    if (lane == 0) pdl_trigger();
   } else {
     // ---------------- epilogue: TMEM -> registers -> C -----------------------
     // C may still be being zero-filled by the kernel this launch depends on
     // (programmatic dependent launch): wait for it before any write to C.
     // Without such a dependency the wait returns at once.
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_wait();
     const int quarter = warp & 3;                  // TMEM lanes 32 quarter .. + 31
     const int part = (warp - 2) >> 2;              // column part of this warp
     constexpr int kParts = kEpiWarps / 4;
@@ -779,7 +784,7 @@ namespace {
 // touching C.
 __global__ void zero_fill_kernel(char* __restrict__ C, int64_t pitch, int64_t row_bytes,
                                  int64_t rows, int vec16) {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  pdl_trigger();   // the tensor-core launch after it starts at once
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     char* row = C + r * pitch;
     if (vec16) {
@@ -823,6 +828,9 @@ rosko_status zero_fill_launch(const ZeroFill& z, cudaStream_t st) {
   // a grid that is resident at once, so that every CTA has signalled its
   // dependents before the tensor-core launch needs an SM
   const int64_t grid = std::min<int64_t>(z.rows, (int64_t)num_sms() * 4);
+  // an ordinary launch: when it starts, every launch before it has completed,
+  // so its programmatic dependent (the tensor-core kernel) may read A and B
+  // at once; only that kernel's writes of C wait for the fill
   zero_fill_kernel<<<(unsigned)grid, 256, 0, st>>>(static_cast<char*>(z.C), z.pitch, z.row_bytes,
                                                    z.rows, vec16);
   count_launches(1);
@@ -920,6 +928,9 @@ rosko_status dense_spmm_launch(const void* dense_A, int64_t dense_rows, int64_t 
   j.ldc = ldc;
   j.M = M;
   j.accumulate = accumulate;
+  // a programmatic dependent of its zero fill only (it reads A and B before
+  // any wait, which is safe only after a launch that started after every
+  // earlier one had completed)
   j.pdl = zf ? 1 : 0;
   return dense_batch_launch(&j, 1, TN, ctas, MH, st);
 }

@@ -662,6 +662,9 @@ __global__ void __launch_bounds__(256, 3)
   using RawT = typename RawOf<CB>::type;
   extern __shared__ __align__(16) unsigned char ring_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // this launch may start while the previous one in the stream finishes
+  // (programmatic dependent launch): wait before reading any global data
+  pdl_wait();
   // the host launches at most 2^31 - 1 items
   const int it = (int)blockIdx.x * 8 + warp;
   if (it >= (int)T.total) return;
@@ -834,6 +837,8 @@ __global__ void __launch_bounds__(256, 3)
     }
     mine = nmine;
   }
+  // the next launch in the stream may be scheduled as this CTA finishes
+  pdl_trigger();
   // C written once (dequantisation needs the scales of this problem)
   SparseParams sp{};
   sp.row_scale = P.row_scale;
@@ -1069,7 +1074,8 @@ static int64_t direct_prob(const DirectJob& j, int V, int64_t items0, DirectProb
   return n_segs * P->strips;
 }
 
-rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaStream_t st) {
+rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaStream_t st,
+                                 bool pdl) {
   if (count <= 0) return ROSKO_OK;
   if (count > 64) return ROSKO_ERR_INVALID_ARG;
   const rosko_dtype a = jobs[0].h->dt, b = jobs[0].b_dt, c = jobs[0].c_dt;
@@ -1108,7 +1114,22 @@ rosko_status direct_batch_launch(const DirectJob* jobs, int count, int V, cudaSt
     const int64_t items = fill(T);
     if (items < 0 || items > INT_MAX) return ROSKO_ERR_UNSUPPORTED;   // 31-bit item index
     if (items == 0) return ROSKO_OK;
-    e->one<<<(unsigned)((items + 7) / 8), 256, e->smem, st>>>(T);
+    if (pdl) {
+      // a programmatic dependent of the launch before it (waits in-kernel)
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)((items + 7) / 8));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = e->smem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      if (cudaLaunchKernelEx(&cfg, e->one, T) != cudaSuccess) return ROSKO_ERR_CUDA;
+    } else {
+      e->one<<<(unsigned)((items + 7) / 8), 256, e->smem, st>>>(T);
+    }
   } else {
     DirectTable<64> T;
     std::memset(static_cast<void*>(&T), 0, sizeof(T));
@@ -1130,7 +1151,7 @@ rosko_status sparse_spmm_launch(rosko_packed_s* h, const void* B, rosko_dtype b_
   if (L.order == 4) {
     // one warp per C row, B from L2; no K split, C written (or added) directly
     DirectJob j{h, B, b_dt, N, ldb, col_scale, C, c_dt, ldc, accumulate, panel_list, n_panels};
-    return direct_batch_launch(&j, 1, L.V, st);
+    return direct_batch_launch(&j, 1, L.V, st, true);
   }
   if (L.order == 2 && !h->rnz) return ROSKO_ERR_UNSUPPORTED;
   if (L.order == 3 && (!h->gnz || L.R != 16 || L.W != 8)) return ROSKO_ERR_UNSUPPORTED;

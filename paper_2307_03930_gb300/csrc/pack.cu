@@ -632,8 +632,7 @@ void plan_dense_tiles(rosko_packed_s* h, int32_t dense_min_pm) {
 // at both granularities: {row, first record, end record, cut} in row order
 // (nat) and, with a panel order, in that order (ord).
 void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32_t>* panel_order,
-                   std::vector<SegEntry> nat[2], std::vector<SegEntry> ord[2],
-                   std::vector<SegEntry> lpt[2]) {
+                   std::vector<int4> nat[2], std::vector<int4> ord[2], std::vector<int4> lpt[2]) {
   const int64_t M = h->M, P = h->P;
   const int64_t lens[2] = {kSegRecords, seg_records_for(h->nnz, M)};
   for (int g = 0; g < 2; ++g) {
@@ -652,11 +651,9 @@ void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32
         const int64_t row_end = (int64_t)rp[r + 1] - 1;
         for (int64_t k = 0; k < ns; ++k) {
           const int64_t e0 = (int64_t)rp[r] + k * seg;
-          SegEntry se;
-          std::memset(&se, 0, sizeof(se));
-          se.head = make_int4((int)r, (int)e0, (int)std::min<int64_t>(e0 + seg, row_end),
-                              ns > 1 ? 1 : 0);
-          nat[g].push_back(se);   // inline records: written on the device
+          // the entry's head; its inline records are written on the device
+          nat[g].push_back(make_int4((int)r, (int)e0, (int)std::min<int64_t>(e0 + seg, row_end),
+                                     ns > 1 ? 1 : 0));
         }
       }
     }
@@ -672,17 +669,19 @@ void plan_segments(rosko_packed_s* h, const int32_t* rp, const std::vector<int32
       L.split[(size_t)i + 1] = L.split[(size_t)i] + panel_split[(size_t)p];
     }
     lpt[g] = nat[g];
-    std::stable_sort(lpt[g].begin(), lpt[g].end(), [](const SegEntry& a, const SegEntry& b) {
-      return a.head.z - a.head.y > b.head.z - b.head.y;
+    std::stable_sort(lpt[g].begin(), lpt[g].end(), [](const int4& a, const int4& b) {
+      return a.z - a.y > b.z - b.y;
     });
   }
 }
 
-// Inline records of the work segments: the first 48 bytes of each piece's
-// records in the row stream (written by the phase-2 launch) copied into its
-// entry; one thread per (segment, 4-byte word), over up to four lists.
+// The work segments' entries: each head (staged from the host, 16 bytes)
+// and the first 48 bytes of the piece's records in the row stream (written
+// by the phase-2 launch); one thread per (segment, 4-byte word: 4 of head,
+// 12 of records), over up to six lists.
 struct InlineLists {
   SegEntry* list[6];
+  const int4* heads[6];
   int64_t n[6];
   int64_t first[7];   // first thread of each list
 };
@@ -692,12 +691,17 @@ __global__ void seg_inline_kernel(InlineLists L, const uint32_t* __restrict__ rn
   while (l < 5 && t >= L.first[l + 1]) ++l;
   if (t >= L.first[6]) return;
   const int64_t local = t - L.first[l];
-  const int64_t s = local / 12;
-  const int w = (int)(local - s * 12);
+  const int64_t s = local / 16;
+  const int w = (int)(local - s * 16);
+  const int4 hd = L.heads[l][s];
   SegEntry& e = L.list[l][s];
-  const int64_t words = (int64_t)(e.head.z - e.head.y) * rec_words;
-  if (w < words && w / rec_words < 12 / rec_words)
-    e.rec[w] = rnz[(int64_t)e.head.y * rec_words + w];
+  if (w < 4) {
+    reinterpret_cast<int*>(&e.head)[w] = w == 0 ? hd.x : (w == 1 ? hd.y : (w == 2 ? hd.z : hd.w));
+    return;
+  }
+  const int rw = w - 4;
+  const int64_t words = (int64_t)(hd.z - hd.y) * rec_words;
+  if (rw < words && rw / rec_words < 12 / rec_words) e.rec[rw] = rnz[(int64_t)hd.y * rec_words + rw];
 }
 
 // Bump allocator over byte offsets, each region 256-byte aligned.
@@ -839,7 +843,7 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
                                               (o_rp - o_sum64))
            : nullptr;
   if (dense) plan_dense_tiles(h, dense_min_pm);
-  std::vector<SegEntry> nat[2], ord[2], lpt[2];
+  std::vector<int4> nat[2], ord[2], lpt[2];
   if (rows) plan_segments(h, rp, dense ? &h->panel_order_host : nullptr, nat, ord, lpt);
 
   const size_t rsz = rec_size(h->dt);
@@ -848,13 +852,14 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
   // staged from the host in one copy
   const size_t o_to = L.take(dense ? (size_t)T * 4 : 0);
   const size_t o_po = L.take(dense ? (size_t)P * 4 : 0);
+  const size_t staged = L.top;
+  // written on the device (the segment entries: heads staged apart, below)
   size_t o_seg[6];
   for (int g = 0; g < 2; ++g) {
     o_seg[3 * g] = L.take(nat[g].size() * sizeof(SegEntry));
     o_seg[3 * g + 1] = L.take(ord[g].size() * sizeof(SegEntry));
     o_seg[3 * g + 2] = L.take(lpt[g].size() * sizeof(SegEntry));
   }
-  const size_t staged = L.top;
   // written on the device
   const size_t o_pc = L.take((size_t)(P + 1) * 4);
   const size_t o_pn = L.take((size_t)(P + 1) * 8);
@@ -903,16 +908,34 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
       std::memcpy(stage.data() + o_to, h->tile_order.data(), (size_t)T * 4);
       std::memcpy(stage.data() + o_po, h->panel_order_host.data(), (size_t)P * 4);
     }
-    for (int g = 0; g < 2; ++g) {
-      if (!nat[g].empty())
-        std::memcpy(stage.data() + o_seg[3 * g], nat[g].data(), nat[g].size() * sizeof(SegEntry));
-      if (!ord[g].empty())
-        std::memcpy(stage.data() + o_seg[3 * g + 1], ord[g].data(), ord[g].size() * sizeof(SegEntry));
-      if (!lpt[g].empty())
-        std::memcpy(stage.data() + o_seg[3 * g + 2], lpt[g].data(), lpt[g].size() * sizeof(SegEntry));
-    }
     // a pageable source is staged before the call returns
     if (cudaMemcpyAsync(b, stage.data(), staged, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return ROSKO_ERR_CUDA;
+  }
+  // the segment heads (16 bytes each; the entries' inline records are
+  // filled on the device) go to stream-ordered scratch from the library's
+  // pool (it keeps freed memory mapped: the default pool would map it anew
+  // on every pack), released after the launch that expands them
+  size_t n_heads = 0;
+  for (int g = 0; g < 2; ++g) n_heads += nat[g].size() + ord[g].size() + lpt[g].size();
+  std::vector<int4> heads;
+  heads.reserve(n_heads);
+  for (int g = 0; g < 2; ++g)
+    for (const std::vector<int4>* v : {&nat[g], &ord[g], &lpt[g]}) heads.insert(heads.end(), v->begin(), v->end());
+  struct Scratch {
+    void* p = nullptr;
+    cudaStream_t st;
+    ~Scratch() {
+      if (p) pool_free(p, st);
+    }
+  } heads_dev{nullptr, st};
+  if (n_heads > 0) {
+    if (pool_malloc(&heads_dev.p, n_heads * sizeof(int4), st) != cudaSuccess) {
+      heads_dev.p = nullptr;
+      return ROSKO_ERR_OOM;
+    }
+    if (cudaMemcpyAsync(heads_dev.p, heads.data(), n_heads * sizeof(int4), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
       return ROSKO_ERR_CUDA;
   }
 
@@ -971,22 +994,22 @@ rosko_status pack_typed(const S* A, int64_t lda, const float* scale_in, bool qua
     InlineLists il;
     std::memset(&il, 0, sizeof(il));
     int nl = 0;
+    // heads are staged in the order nat, ord, lpt of list 0, then of list 1
+    const int4* hp = static_cast<const int4*>(heads_dev.p);
     for (int g = 0; g < 2; ++g) {
-      if (h->segs[g].nat && !nat[g].empty()) {
-        il.list[nl] = h->segs[g].nat;
-        il.n[nl++] = (int64_t)nat[g].size();
-      }
-      if (h->segs[g].ord && !ord[g].empty()) {
-        il.list[nl] = h->segs[g].ord;
-        il.n[nl++] = (int64_t)ord[g].size();
-      }
-      if (h->segs[g].lpt && !lpt[g].empty()) {
-        il.list[nl] = h->segs[g].lpt;
-        il.n[nl++] = (int64_t)lpt[g].size();
+      SegEntry* dst[3] = {h->segs[g].nat, h->segs[g].ord, h->segs[g].lpt};
+      const std::vector<int4>* src[3] = {&nat[g], &ord[g], &lpt[g]};
+      for (int k = 0; k < 3; ++k) {
+        if (dst[k] && !src[k]->empty()) {
+          il.list[nl] = dst[k];
+          il.heads[nl] = hp;
+          il.n[nl++] = (int64_t)src[k]->size();
+        }
+        hp += src[k]->size();
       }
     }
     il.first[0] = 0;
-    for (int l = 0; l < 6; ++l) il.first[l + 1] = il.first[l] + (l < nl ? il.n[l] * 12 : 0);
+    for (int l = 0; l < 6; ++l) il.first[l + 1] = il.first[l] + (l < nl ? il.n[l] * 16 : 0);
     if (il.first[6] > 0) {
       seg_inline_kernel<<<(unsigned)((il.first[6] + 255) / 256), 256, 0, st>>>(
           il, static_cast<const uint32_t*>(h->rnz), (int)(rsz / 4));

@@ -851,8 +851,9 @@ rosko_status dense_spmm_i8_launch(const rosko_packed_s* h, int64_t n_tiles, cons
   const int64_t K = h->K;
   const int64_t ldo = (N + 7) / 8 * 8;   // 16-byte rows for the tensor map
   void* scratch = nullptr;
-  // stream-ordered (and capturable): released after the launch that reads it
-  if (cudaMallocAsync(&scratch, (size_t)std::max<int64_t>(K * ldo, 1) * 2, st) != cudaSuccess)
+  // stream-ordered (and capturable) from the library's pool, which keeps
+  // freed memory mapped: released after the launch that reads it
+  if (pool_malloc(&scratch, (size_t)std::max<int64_t>(K * ldo, 1) * 2, st) != cudaSuccess)
     return ROSKO_ERR_OOM;
   const int64_t work = K * ((ldo + 3) / 4);
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096));
@@ -883,7 +884,7 @@ rosko_status dense_spmm_i8_launch(const rosko_packed_s* h, int64_t n_tiles, cons
     j.pdl = zf ? 1 : 0;
     s = dense_batch_launch(&j, 1, TN, ctas, MH, st);
   }
-  cudaFreeAsync(scratch, st);
+  pool_free(scratch, st);
   return s;
 }
 

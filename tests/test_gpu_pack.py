@@ -118,18 +118,18 @@ def test_pack_empty_shapes():
 
 
 def test_alloc_failure_is_reported(monkeypatch):
-    # host-side fault injection: each of the packer's two device allocations
-    # (pass-1 scratch, then the handle) fails in turn and is reported as
-    # ROSKO_ERR_OOM; there is no third
+    # host-side fault injection: each of the packer's three device
+    # allocations (pass-1 scratch, the handle, the segment-head scratch)
+    # fails in turn and is reported as ROSKO_ERR_OOM; there is no fourth
     rosko = built()
     A = torch.randn(40, 40, device="cuda")
-    for n in ("1", "2"):
+    for n in ("1", "2", "3"):
         monkeypatch.setenv("ROSKO_FAIL_ALLOC", n)
         with pytest.raises(rosko.RoskoError) as ei:
             rosko.rosko_pack(A, 0)
         assert ei.value.status == 3
     for dt in (rosko.F32, rosko.BF16):
-        monkeypatch.setenv("ROSKO_FAIL_ALLOC", "3" if dt == rosko.F32 else "4")
+        monkeypatch.setenv("ROSKO_FAIL_ALLOC", "4" if dt == rosko.F32 else "5")
         h = rosko.rosko_pack(A, dt)
         assert h.info()["nnz"] == int((A != 0).sum())
     monkeypatch.delenv("ROSKO_FAIL_ALLOC")

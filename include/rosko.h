@@ -183,8 +183,17 @@ rosko_status rosko_pack_transposed(const void* A_dev, rosko_dtype a_dtype, int64
  * chunk of at most 1024 sums below 2^24 in magnitude (exact in the FP32
  * accumulator) and is added into C as INT32, so the result is bit-identical
  * to the integer sum; the call converts B to BF16 in stream-ordered scratch
- * (K x N x 2 bytes, cudaMallocAsync / cudaFreeAsync on `stream`).  The FP32
- * (dequantised) INT8 result stays on the CUDA-core path.
+ * (K x N x 2 bytes from the library's device memory pool on `stream`,
+ * released in stream order).  The FP32 (dequantised) INT8 result stays on
+ * the CUDA-core path.
+ * Stream order: when C must be zero-filled first (tiles or rows cut along K
+ * and added), the fill is a small kernel ahead of a tensor-core launch, else
+ * a memset.  The tensor-core kernel is launched as a programmatic dependent
+ * of that fill (it reads A and B at once and writes C only after the fill),
+ * and the row-direct kernel as a programmatic dependent of whatever kernel
+ * precedes it on `stream` (it reads nothing before that kernel has
+ * completed).  Both keep ordinary stream-order semantics for the caller;
+ * they only let the launch overlap its predecessor's tail.
  * The row-direct traversal numbers its work items (row pieces x column
  * strips of n_r columns) with 31 bits; beyond that it returns
  * ROSKO_ERR_UNSUPPORTED.

@@ -94,3 +94,46 @@ def test_analytic_schedule_fits_gb300(M, K, N, s, dt):
     P = -(-M // t["m_r"])
     ctas = -(-P // (t["m_c"] // t["m_r"])) * -(-N // t["n_r"]) * t["split_k"]
     assert ctas >= min(152, -(-P // (t["m_c"] // t["m_r"])) * -(-N // t["n_r"]))
+
+
+def test_tensor_core_tile_rules():
+    # host-only: the analytic schedule's tensor-core tile (GB300, 152 SMs)
+    rosko = built()
+
+    def sched(M, K, N, s, dt):
+        return rosko.rosko_schedule_analytic(M, K, N, int(M * K * (1 - s)), 0, dt)
+
+    # enough K work per CTA (>= 20 double slabs): 256-row tiles, stream-K
+    # over every SM
+    t = sched(1024, 4096, 4096, 0.9, rosko.BF16)
+    assert (t["dense_m_c"], t["dense_n_r"], t["dense_split_k"]) == (256, 256, 152)
+    t = sched(11008, 4096, 2048, 0.7, rosko.BF16)
+    assert t["dense_m_c"] == 256
+    # INT8 codes drain the accumulator every 1,024 K: 128 rows, so that the
+    # second TMEM set overlaps the drains
+    t = sched(11008, 4096, 2048, 0.7, rosko.I8)
+    assert t["dense_m_c"] == 128
+    # 512x4608x3136: 12 double slabs per CTA -> 128-row tiles; its 52 tiles
+    # are far from filling the GPU -> split along K over every SM
+    t = sched(512, 4608, 3136, 0.9, rosko.BF16)
+    assert (t["dense_m_c"], t["dense_n_r"], t["dense_split_k"]) == (128, 256, 152)
+    # 2048^3: 128 tiles nearly fill the GPU -> one whole tile per CTA
+    t = sched(2048, 2048, 2048, 0.9, rosko.BF16)
+    assert (t["dense_m_c"], t["dense_split_k"]) == (128, 128)
+    # K < 1024 (fewer than 16 slabs): whole 128-wide tiles, one per CTA up
+    # to two per SM
+    t = sched(1024, 512, 4096, 0.9, rosko.BF16)
+    assert (t["dense_n_r"], t["dense_m_c"], t["dense_split_k"]) == (128, 128, 8 * 32)
+
+
+def test_split_rule_follows_the_two_time_models():
+    # 512x4608x3136: row-direct predicted faster at 99 % (the layer stays
+    # sparse), the tensor cores at 90 % (tiles of >= 15 per mille go dense)
+    rosko = built()
+    t = rosko.rosko_schedule_analytic(512, 4608, 3136, int(512 * 4608 * 0.01), 0, rosko.BF16)
+    assert t["dense_split_pm"] == 1001 and t["order"] == 4
+    t = rosko.rosko_schedule_analytic(512, 4608, 3136, int(512 * 4608 * 0.1), 0, rosko.BF16)
+    assert t["dense_split_pm"] == 15
+    # FP32 packs have no tensor-core path
+    t = rosko.rosko_schedule_analytic(512, 4608, 3136, int(512 * 4608 * 0.1), 0, rosko.F32)
+    assert t["dense_split_pm"] == 1001

@@ -24,7 +24,12 @@
 // row tiles) still fill every SM in one wave.  A share covers the K ranges of
 // one or two tiles; two TMEM accumulators alternate so that the epilogue of
 // one range overlaps the MMAs of the next.  A tile whose K range is cut
-// between CTAs is added into C; a tile owned whole is stored.
+// between CTAs is added into C; a tile owned whole is stored.  C is then
+// zero-filled by a small kernel launched just before this one, of which this
+// launch is a programmatic dependent: the ring fills and MMAs start at once
+// and only the epilogue waits (griddepcontrol.wait) for the fill, which thus
+// runs under the MMAs.  The first ring fill is issued by thread 0 before the
+// TMEM allocation and the block barrier, overlapping its cold DRAM latency.
 //
 // Epilogue: each epilogue warp moves its 32 TMEM lanes (C rows) 32 columns
 // at a time into a 32 x 32 FP32 staging tile in shared memory (128-byte
